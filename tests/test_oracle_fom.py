@@ -1,0 +1,55 @@
+"""Pins of the oracle's implicit trapezoid FOM (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle import direct, fom, qoi
+from paper_2103_01983_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("mode", ["dense", "blockdiag", "jfnk"])
+def test_two_vortex_trapezoid_rotation(mode):
+    """The trapezoid rule maps the relative vector by a Cayley transform:
+    |r| is kept and the angle advances by exactly 2 atan(omega dt / 2)."""
+    d, delta, g1, g2, dt = 0.8, 0.05, 1.0, 1.0, 0.1
+    x, G = W.two_vortex(d, g1, g2)
+    omega = (g1 + g2) / (2 * np.pi * (d * d + delta))
+    traj, _ = fom.rollout(x, G, delta, dt, 10, mode=mode, tol=1e-14)
+    r = np.stack([traj[:, 1] - traj[:, 0], traj[:, 3] - traj[:, 2]], axis=1)
+    ang = np.unwrap(np.arctan2(r[:, 1], r[:, 0]))
+    np.testing.assert_allclose(np.diff(ang), 2 * np.arctan(omega * dt / 2), rtol=1e-11)
+    np.testing.assert_allclose(np.hypot(r[:, 0], r[:, 1]), d, rtol=1e-12)
+    # Gamma-weighted centroid is fixed
+    c = (g1 * traj[:, [0, 2]] + g2 * traj[:, [1, 3]]) / (g1 + g2)
+    np.testing.assert_allclose(c, 0.0, atol=1e-13)
+
+
+def test_modes_agree_and_impulse_conserved():
+    x, G = W.disk(128, seed=11)
+    delta, dt = 0.05, 0.01
+    out = {}
+    for mode in ["dense", "blockdiag", "jfnk"]:
+        traj, it = fom.rollout(x, G, delta, dt, 5, mode=mode, tol=1e-13)
+        out[mode] = traj
+        P = np.array([qoi.linear_impulse(s, G) for s in traj])
+        # sum_i Gamma_i r_i = P(x^n) - P(x^{n-1}) because sum_i Gamma_i f_i = 0,
+        # so the drift per step is bounded by |Gamma|_2 * ||r||_2 <= |Gamma|_2 tol |x|
+        bound = np.linalg.norm(G) * 1e-13 * np.linalg.norm(traj, axis=1).max() * 5 + 1e-14
+        np.testing.assert_allclose(P, np.broadcast_to(P[0], P.shape), rtol=0, atol=bound)
+    np.testing.assert_allclose(out["blockdiag"], out["dense"], atol=1e-11)
+    np.testing.assert_allclose(out["jfnk"], out["dense"], atol=1e-11)
+
+
+def test_residual_zero_at_solution():
+    x, G = W.disk(64, seed=12)
+    delta, dt = 0.05, 0.01
+    f0 = direct.velocity(x, G, delta)
+    x1, f1, k, rn = fom.step(x, f0, G, delta, dt, mode="dense", tol=1e-14)
+    r = x1 - x - 0.5 * dt * (direct.velocity(x1, G, delta) + f0)
+    assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(x1)
+    np.testing.assert_allclose(f1, direct.velocity(x1, G, delta), rtol=0, atol=0)
+
+
+def test_hamiltonian_two_vortex():
+    """H = Gamma1 Gamma2 log(d) / (2 pi) for two bodies (both ordered pairs)."""
+    x, G = W.two_vortex(2.5, 1.5, -0.7)
+    assert qoi.hamiltonian(x, G) == pytest.approx(1.5 * -0.7 * np.log(2.5) / (2 * np.pi), rel=1e-14)
