@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the PTROM hot path on GB300.
+
+One step = one implicit trapezoid FOM step (Sec. 2, Eq. linKstep) of the
+two-Gaussian-cluster workload (N=16384, delta=0.02, dt=0.005), solved by
+Jacobian-free Newton-Krylov: the velocity with self blocks (inexact Jacobian
+for the preconditioner), the J v products inside GMRES, the residual and the
+FP64 state update -- all in libptrom.so.  The metric is Biot-Savart pair
+evaluations per second: (velocity + J v launches) x N^2 pairs per step.
+
+Inputs are synthetic (seeded generator), resident in HBM when the timed
+region starts; the 129 MB L2 is flushed (256 MB memset) before every timed
+step.  With --impl reference the FP64 CPU oracle is timed instead on the host
+cores (a bounded sample of the same workload).
+
+Multi-GPU: every rank runs an independent replica (the FOM step of one
+instance does not shard on this hardware); value = all ranks' pairs / the
+slowest rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Biot-Savart pair evals/s"
+UNIT = "pairs/s"
+WORKLOAD = {
+    "workload": "two-cluster FOM implicit trapezoid step, JFNK (GMRES on J v), FP32C pair sums",
+    "n_bodies": 16384,
+    "delta": 0.02,
+    "dt": 0.005,
+    "clusters": "2 Gaussian, std 0.1, centres 1.0 apart, circulation ratio 1:1",
+    "newton_tol": 1e-8,
+    "gmres": "restart 30, rtol 1e-4, block-diagonal right preconditioner",
+    "l2": "flushed (256 MB memset) before every timed step",
+}
+# Algorithmic FP32 flops per pair (an FMA counts 2, the reciprocal 1); the
+# derivation per kernel is in the design doc.
+FLOPS_PER_PAIR = {"velocity": 12, "velocity_selfjac": 24, "jvp": 23, "vjp": 31}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count, sm_mhz):
+    """FP32 non-tensor peak: SMs x 128 lanes x 2 flop (FMA) x clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.index)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    return rank, local, ws
+
+
+# --------------------------------------------------------------------- oracle
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores: per step, the pair sums one FOM
+    Newton iteration makes (velocity + self blocks, 8 J v products) on a
+    bounded sample of 512 target rows against all 16384 sources."""
+    import numpy as np
+
+    from oracle import direct
+    from paper_2103_01983_gb300 import workloads as W
+
+    n = WORKLOAD["n_bodies"]
+    x, G = W.two_cluster(n, seed=0)
+    rows = np.random.default_rng(0).choice(n, 512, replace=False)
+    idx = np.r_[rows, n + rows]
+    v = W.random_vectors(2 * n, 1, seed=1)[0]
+
+    def step():
+        direct.velocity(x, G, WORKLOAD["delta"], targets=x[idx], with_selfjac=True)
+        for _ in range(8):
+            direct.jvp(x, G, WORKLOAD["delta"], v, rows=rows)
+        return 9 * rows.size * n
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    pairs = 0
+    for _ in range(args.steps):
+        pairs += step()
+    dt = time.perf_counter() - t0
+    value = pairs / dt
+    cores = direct.num_threads()
+    sample = "per step: velocity+self blocks and 8 J v products at 512 sampled targets x 16384 sources (FP64 C loops)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": WORKLOAD,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline(budget_s=12.0):
+    """Oracle pair throughput on the host cores (bounded sample, FP64)."""
+    import numpy as np
+
+    from oracle import direct
+    from paper_2103_01983_gb300 import workloads as W
+
+    n = WORKLOAD["n_bodies"]
+    x, G = W.two_cluster(n, seed=0)
+    v = W.random_vectors(2 * n, 1, seed=1)[0]
+    rows = np.random.default_rng(0).choice(n, 1024, replace=False)
+    idx = np.r_[rows, n + rows]
+    pairs, t0, reps = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s:
+        direct.velocity(x, G, WORKLOAD["delta"], targets=x[idx], with_selfjac=True)
+        for _ in range(4):
+            direct.jvp(x, G, WORKLOAD["delta"], v, rows=rows)
+        pairs += 5 * rows.size * n
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": UNIT, "cores": direct.num_threads(), "kind": "oracle",
+            "sample": f"{reps} x (velocity+self blocks and 4 J v products) at 1024 sampled targets "
+                      f"x {n} sources, FP64, {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local, ws = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2103_01983_gb300 import ptrom
+    from paper_2103_01983_gb300 import workloads as W
+
+    n, delta, dt = WORKLOAD["n_bodies"], WORKLOAD["delta"], WORKLOAD["dt"]
+    x0, G = W.two_cluster(n, seed=0)
+    x = torch.tensor(x0, device=dev)
+    Gt = torch.tensor(G, device=dev)
+    params = ptrom.fom_params(dt, delta, "jfnk", tol=WORKLOAD["newton_tol"], prec="fp32c",
+                              gmres_restart=30, gmres_max_iter=200, gmres_rtol=1e-4)
+    f = ptrom.bs_velocity(x, Gt, delta)
+    work = ptrom.fom_workspace(params, n, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ptrom.fom_step(params, Gt, x, f, work=work)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.25)
+    ptrom.timing_read()
+    ptrom.timing_enable(True)
+    l0 = ptrom.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    agg = {"velocity_evals": 0, "jvp_evals": 0, "newton_iters": 0, "linear_iters": 0}
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        st = ptrom.fom_step(params, Gt, x, f, work=work)
+        ev[k][1].record(stream)
+        for key in agg:
+            agg[key] += st[key]
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    launches = ptrom.launch_count() - l0  # the L2-flush memsets are torch's, not counted
+    ptrom.timing_enable(False)
+    ktimes = ptrom.timing_read()
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    pairs = (agg["velocity_evals"] + agg["jvp_evals"]) * n * n
+
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(pairs)], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms_all, pairs_all = float(tmax[0]), float(t[1])
+    else:
+        ms_all, pairs_all = ms, float(pairs)
+    value = pairs_all / (ms_all * 1e-3)
+
+    # roofline of the dominant kernel (largest event-timed total)
+    peaks, peak_src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_count, sm_mhz)
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms, dom_cnt = ktimes[dom]
+    achieved = FLOPS_PER_PAIR[dom] * n * n * dom_cnt / (dom_ms * 1e-3) / 1e12 if dom_cnt else None
+    traffic = _traffic(dom)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "peak_source": f"{peak_src}: {sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                "flops_per_pair": FLOPS_PER_PAIR[dom],
+                "launches": dom_cnt, "avg_launch_us": 1e3 * dom_ms / dom_cnt if dom_cnt else None}
+    kernels = {k: {"launches": c, "avg_us": 1e3 * t / c,
+                   "pairs_per_s": n * n * c / (t * 1e-3),
+                   "tflops": FLOPS_PER_PAIR[k] * n * n * c / (t * 1e-3) / 1e12}
+               for k, (t, c) in ktimes.items() if c}
+
+    # end to end: host buffers, H2D of the step's inputs and D2H of its result
+    e2e = _e2e(args, ptrom, params, x0, G, dev, stream, n)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair sums (compensated), f64 state",
+        "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"),
+        "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+        "step_stats": {k: v / args.steps for k, v in agg.items()},
+        "kernels": kernels,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def _traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, when it exists."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh).get(kind)
+    except (OSError, ValueError):
+        return None
+
+
+def _e2e(args, ptrom, params, x0, G, dev, stream, n):
+    import torch
+
+    xh = torch.tensor(x0).pin_memory()
+    Gh = torch.tensor(G).pin_memory()
+    x = torch.empty_like(xh, device=dev)
+    Gd = torch.empty_like(Gh, device=dev)
+    x.copy_(xh)
+    Gd.copy_(Gh)
+    fh = ptrom.bs_velocity(x, Gd, params.delta).cpu().pin_memory()
+    f = torch.empty_like(fh, device=dev)
+    work = ptrom.fom_workspace(params, n, dev)
+    steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    pairs = 0
+    t0.record(stream)
+    for _ in range(steps):
+        x.copy_(xh, non_blocking=True)
+        f.copy_(fh, non_blocking=True)
+        Gd.copy_(Gh, non_blocking=True)
+        st = ptrom.fom_step(params, Gd, x, f, work=work)
+        xh.copy_(x, non_blocking=True)
+        fh.copy_(f, non_blocking=True)
+        pairs += (st["velocity_evals"] + st["jvp_evals"]) * n * n
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    nb = xh.numel() * 8
+    return {"value": pairs / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * nb + Gh.numel() * 8,
+            "d2h_bytes_per_step": 2 * nb, "steps": steps,
+            "note": "public API (ptrom.fom_step) from pinned host buffers; x, f, Gamma H2D and x, f D2H every step"}
+
+
+def kernel_only(args):
+    """Launch one all-pairs kernel `args.steps` times at N = args.n (for ncu)."""
+    import torch
+
+    from paper_2103_01983_gb300 import ptrom
+    from paper_2103_01983_gb300 import workloads as W
+
+    x0, G = W.two_cluster(args.n, seed=0)
+    x = torch.tensor(x0, device="cuda")
+    Gt = torch.tensor(G, device="cuda")
+    v = torch.tensor(W.random_vectors(2 * args.n, 1, seed=1)[0], device="cuda")
+    fn = {"velocity": lambda: ptrom.bs_velocity(x, Gt, 0.02),
+          "velocity_selfjac": lambda: ptrom.bs_velocity(x, Gt, 0.02, selfjac=True),
+          "jvp": lambda: ptrom.bs_jvp(x, Gt, 0.02, v),
+          "vjp": lambda: ptrom.bs_vjp(x, Gt, 0.02, v)}[args.kernel_only]
+    for _ in range(args.warmup + args.steps):
+        fn()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_only": args.kernel_only, "n": args.n, "launches": args.warmup + args.steps}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp"],
+                    help="profiling aid: launch only this kernel (no JSON metric line)")
+    ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")
+    args = ap.parse_args()
+    if args.kernel_only:
+        kernel_only(args)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return
+        args.steps = min(args.steps, 20)
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+    line = run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

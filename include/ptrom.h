@@ -1,0 +1,191 @@
+/*
+ * ptrom.h -- C ABI of libptrom.so, the GB300 (sm_103a) implementation of the
+ * projection-tree reduced-order model's hot path (arXiv 2103.01983).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - State layout (Sec. 2, Eq. 3): a state of n bodies is a length-2n FP64
+ *    array x = [chi_1..chi_n, psi_1..psi_n]; velocities f use the same layout.
+ *  - Circulations Gamma (length n, FP64) are the paper's Gamma_j; the factor
+ *    1/(2 pi) of Eq. 2 is applied inside the library.
+ *  - Unless a parameter says "host", every pointer is a DEVICE pointer
+ *    allocated and owned by the caller; the library keeps no reference to it
+ *    after the call returns.  Device buffers must be 8-byte aligned.
+ *  - Every call is enqueued on the caller's CUDA stream `stream` (0 = the
+ *    legacy default stream) and returns without synchronising, unless its
+ *    comment says it synchronises (solvers that must read a convergence flag).
+ *  - Every function returns a status: 0 (PTROM_OK) or a negative code below.
+ *    On error nothing has been enqueued unless the code is PTROM_ECUDA (a CUDA
+ *    error was reported while enqueuing or synchronising).  ptrom_last_error()
+ *    returns a one-line description of the calling thread's last error.
+ *  - Precision `prec`: PTROM_FP32C computes pair terms in FP32 and accumulates
+ *    them with compensated (TwoSum) sums; inputs/outputs stay FP64.
+ *    PTROM_FP64 computes everything in FP64 (slow on GB300; for checking).
+ *  - A pair (i, j) whose positions coincide exactly is skipped in every sum:
+ *    that is the j != i restriction of Eq. 1 (and a coincident body).
+ */
+#ifndef PTROM_H
+#define PTROM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ptrom_stream_t; /* same type as cudaStream_t */
+
+enum ptrom_status {
+    PTROM_OK = 0,
+    PTROM_EINVAL = -1,   /* bad argument (size, pointer, option)           */
+    PTROM_ECUDA = -2,    /* a CUDA runtime call failed                     */
+    PTROM_ENOCONV = -3,  /* iteration limit reached before the tolerance   */
+    PTROM_ENAN = -4,     /* a NaN/Inf appeared in a residual               */
+    PTROM_ETIMEOUT = -5, /* a device-side bounded wait gave up             */
+    PTROM_ENOMEM = -6    /* a workspace was too small or allocation failed */
+};
+
+enum ptrom_prec { PTROM_FP32C = 0, PTROM_FP64 = 1 };
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len) and returns the status it came with. */
+int ptrom_last_error(char *buf, size_t len);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int ptrom_version(void);
+
+/* Tuning override for the all-pairs kernels: split every launch's sources
+ * over S CTAs of one thread-block cluster (1 <= S <= 8), or S = 0 to restore
+ * the automatic choice (the default).  Process-wide; results are identical up
+ * to FP rounding for every S.  Returns PTROM_EINVAL for S outside [0, 8]. */
+int ptrom_set_source_split(int S);
+
+/* Instrumentation (host-side, process-wide).
+ * ptrom_launch_count: number of CUDA kernels the library has launched so far.
+ * ptrom_timing_enable(1): from now on every all-pairs launch is bracketed by
+ *   two CUDA events recorded on the launch's own stream (up to 65536 launches;
+ *   later ones are not timed); ptrom_timing_enable(0) stops recording.
+ * ptrom_timing_read: synchronises the recorded events and returns, for each
+ *   kernel kind k < nkinds (enum ptrom_kernel_kind), the summed device time in
+ *   milliseconds (ms[k]) and the number of timed launches (count[k]); then
+ *   forgets them.  Returns PTROM_EINVAL for NULL arrays or nkinds < 1. */
+enum ptrom_kernel_kind {
+    PTROM_K_VELOCITY = 0,      /* bs_velocity without self blocks */
+    PTROM_K_VELOCITY_D = 1,    /* bs_velocity with self blocks    */
+    PTROM_K_JVP = 2,
+    PTROM_K_VJP = 3,
+    PTROM_K_JPHI = 4,
+    PTROM_K_PTROM_STEP = 5,
+    PTROM_K_NKINDS = 6
+};
+long long ptrom_launch_count(void);
+int ptrom_timing_enable(int on);
+int ptrom_timing_read(double *ms, long long *count, int nkinds);
+
+/*
+ * bs_velocity -- regularised Biot-Savart velocity (Sec. 2, Eq. 1-2):
+ *     f_i = sum_{j != i} Gamma_j/(2 pi) e3 x (t_i - s_j) / (|t_i - s_j|^2 + delta)
+ * for nt targets t (xt, length 2*nt) and ns sources s (xs, length 2*ns,
+ * strengths Gamma, length ns).  Targets may be the sources themselves
+ * (xt == xs, nt == ns) or any other points (e.g. grid vertices, Sec. 6.1).
+ *   f_out        [2*nt]  velocity at the targets.
+ *   selfjac_out  [3*nt]  optional (NULL to skip): the per-target 2x2 block
+ *                d f_i / d t_i = sum_j gamma_j A(t_i - s_j), the "diagonal
+ *                block entries" of the inexact kernel Jacobian (Sec. 2, last
+ *                paragraph), stored as [D00 (nt) | D01 (nt) | D10 (nt)];
+ *                D11 = -D00 (the block is trace-free).
+ * Errors: nt < 1 or ns < 1, delta < 0, NULL arrays, bad prec -> PTROM_EINVAL.
+ */
+int bs_velocity(int nt, const double *xt, int ns, const double *xs,
+                const double *Gamma, double delta, double *f_out,
+                double *selfjac_out, int prec, ptrom_stream_t stream);
+
+/*
+ * bs_jvp -- Jacobian-vector product of the kernel, jv = (d f / d x) v, with
+ * all blocks (the exact Jacobian whose product the Gauss-Newton/LSPG step of
+ * Sec. 3.2 and a Jacobian-free Newton solve of Eq. linKstep need):
+ *     (J v)_i = sum_{j != i} gamma_j A(x_i - x_j) (v_i - v_j),  gamma = Gamma/(2 pi).
+ * x, v, jv: [2n]; Gamma: [n].  Errors as bs_velocity (n < 2 -> PTROM_EINVAL).
+ */
+int bs_jvp(int n, const double *x, const double *Gamma, double delta,
+           const double *v, double *jv, int prec, ptrom_stream_t stream);
+
+/*
+ * bs_vjp -- transposed products (adjoint of Sec. 2's kernel):
+ *     gx = (d f / d x)^T w,     (J^T w)_k = sum_j A(x_k - x_j)^T (gamma_j w_k - gamma_k w_j)
+ *     gGamma = (d f / d Gamma)^T w,   gGamma_k = sum_i w_i . e3 x (x_i - x_k) / (2 pi s_ik)
+ * Either output may be NULL (not computed).  x, w, gx: [2n]; Gamma, gGamma: [n].
+ */
+int bs_vjp(int n, const double *x, const double *Gamma, double delta,
+           const double *w, double *gx_out, double *gGamma_out, int prec,
+           ptrom_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Full-order model (FOM): one implicit trapezoid step (Sec. 2, Eq. linKstep
+ * with k=1, alpha0=1, alpha1=-1, beta0=beta1=1/2):
+ *     r(xi) = xi - x^{n-1} - dt/2 (f(xi) + f(x^{n-1})) = 0,
+ * solved by Newton from xi = x^{n-1}; each iteration solves
+ * (I - dt/2 J) d = -r and sets xi += d, with J chosen by jac_mode:
+ *   PTROM_JAC_BLOCKDIAG  only the per-body 2x2 self blocks d f_i/d x_i: the
+ *                        paper's inexact kernel Jacobian (Sec. 2);
+ *   PTROM_JAC_DENSE      the full 2n x 2n Jacobian, assembled in FP64 and
+ *                        LU-factorised with partial pivoting (n <= 4096);
+ *   PTROM_JAC_JFNK       the full Jacobian applied matrix-free through the
+ *                        J v kernel inside restarted GMRES, right-
+ *                        preconditioned by the block-diagonal Jacobian.
+ * The Jacobian (self blocks / dense factors) is refreshed every p_it Newton
+ * iterations.  Convergence: ||r||_2 <= tol * max(1, ||xi||_2), checked after
+ * each evaluation of f(xi) (so the returned f is f at the returned state).
+ * ------------------------------------------------------------------------ */
+enum ptrom_jac_mode { PTROM_JAC_BLOCKDIAG = 0, PTROM_JAC_DENSE = 1, PTROM_JAC_JFNK = 2 };
+
+typedef struct ptrom_fom_params {
+    double dt;          /* time step (> 0)                                   */
+    double delta;       /* de-singularisation constant delta_k of Eq. 2     */
+    double tol;         /* Newton tolerance (see above)                     */
+    int max_iter;       /* Newton iteration cap (the paper uses 100)         */
+    int jac_mode;       /* enum ptrom_jac_mode                               */
+    int p_it;           /* Jacobian refresh period in Newton iterations >= 1 */
+    int prec;           /* pair-sum precision, enum ptrom_prec               */
+    int gmres_restart;  /* JFNK: Krylov vectors per cycle, 1..64             */
+    int gmres_max_iter; /* JFNK: Krylov iterations per Newton step           */
+    double gmres_rtol;  /* JFNK: relative linear tolerance                   */
+} ptrom_fom_params;
+
+typedef struct ptrom_fom_stats {
+    int newton_iters;   /* Newton iterations taken (solves performed)        */
+    int linear_iters;   /* total GMRES iterations (JFNK)                     */
+    int velocity_evals; /* all-pairs velocity launches                       */
+    int jvp_evals;      /* all-pairs J v launches                            */
+    double res_norm;    /* ||r||_2 at the returned state                     */
+    double res_norm0;   /* ||r||_2 at xi = x^{n-1}                           */
+} ptrom_fom_stats;
+
+/* Device workspace (bytes) fom_step needs for these parameters and n. */
+size_t fom_workspace_bytes(const ptrom_fom_params *p, int n);
+
+/*
+ * fom_step -- advance one implicit trapezoid step.
+ *   p      host pointer to the parameters.
+ *   Gamma  [n] circulations.
+ *   x      [2n] in: x^{n-1}; out: x^n (the last Newton iterate).
+ *   f      [2n] in: f(x^{n-1}); out: f(x^n).
+ *   work   device workspace of at least fom_workspace_bytes(p, n) bytes,
+ *          256-byte aligned, owned by the caller; its contents on entry do not
+ *          matter.  Calls that share one workspace must not overlap in time.
+ *   stats  optional host pointer (NULL to skip).
+ * Synchronises `stream` once per Newton iteration (to read ||r||) and once
+ * per GMRES iteration.  Returns PTROM_ENOCONV if max_iter iterations did not
+ * reach tol (x, f then hold the last iterate), PTROM_ENAN on a non-finite
+ * residual, PTROM_EINVAL for bad parameters (n < 2, dt <= 0, delta < 0,
+ * dense mode with n > 4096, work too small).
+ */
+int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x,
+             double *f, void *work, size_t work_bytes, ptrom_fom_stats *stats,
+             ptrom_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTROM_H */

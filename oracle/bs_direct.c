@@ -24,6 +24,7 @@
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -76,12 +77,14 @@ void or_velocity(int nt, const double *xt, int ns, const double *xs,
 }
 
 /* J v with J = d f / d x (all blocks, Sec. 3.2 Jacobian of the kernel):
- * (J v)_i = D_i v_i + sum_{j != i} (-gamma_j A(x_i - x_j)) v_j. */
-void or_jvp(int n, const double *x, const double *Gamma, double delta,
-            const double *v, double *jv) {
-    int i;
+ * (J v)_i = D_i v_i + sum_{j != i} (-gamma_j A(x_i - x_j)) v_j.
+ * or_jvp_rows evaluates only the rows (bodies) listed in rows[0..nrows). */
+void or_jvp_rows(int n, const double *x, const double *Gamma, double delta,
+                 const double *v, const int *rows, int nrows, double *jv) {
+    int r;
 #pragma omp parallel for schedule(static)
-    for (i = 0; i < n; ++i) {
+    for (r = 0; r < nrows; ++r) {
+        int i = rows[r];
         double D[4] = {0.0, 0.0, 0.0, 0.0};
         double off0 = 0.0, off1 = 0.0;
         for (int j = 0; j < n; ++j) {
@@ -95,9 +98,17 @@ void or_jvp(int n, const double *x, const double *Gamma, double delta,
             off0 += -g * (A[0] * v[j] + A[1] * v[n + j]);
             off1 += -g * (A[2] * v[j] + A[3] * v[n + j]);
         }
-        jv[i] = D[0] * v[i] + D[1] * v[n + i] + off0;
-        jv[n + i] = D[2] * v[i] + D[3] * v[n + i] + off1;
+        jv[r] = D[0] * v[i] + D[1] * v[n + i] + off0;
+        jv[nrows + r] = D[2] * v[i] + D[3] * v[n + i] + off1;
     }
+}
+
+void or_jvp(int n, const double *x, const double *Gamma, double delta,
+            const double *v, double *jv) {
+    int *rows = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; ++i) rows[i] = i;
+    or_jvp_rows(n, x, Gamma, delta, v, rows, n, jv);
+    free(rows);
 }
 
 /* Transposed products.
@@ -105,11 +116,12 @@ void or_jvp(int n, const double *x, const double *Gamma, double delta,
  *                              = D_k^T w_k + sum_{i != k} (-gamma_k A(x_i - x_k))^T w_i
  * gG (n, optional):   (d f / d Gamma)^T w, i.e.
  *                     gG_k = sum_{i != k} w_i . (1/(2 pi)) e3 x (x_i - x_k) / s_ik */
-void or_vjp(int n, const double *x, const double *Gamma, double delta,
-            const double *w, double *gx, double *gG) {
-    int k;
+void or_vjp_rows(int n, const double *x, const double *Gamma, double delta,
+                 const double *w, const int *rows, int nrows, double *gx, double *gG) {
+    int r;
 #pragma omp parallel for schedule(static)
-    for (k = 0; k < n; ++k) {
+    for (r = 0; r < nrows; ++r) {
+        int k = rows[r];
         double D[4] = {0.0, 0.0, 0.0, 0.0};
         double t0 = 0.0, t1 = 0.0, gg = 0.0;
         double gk = Gamma[k] / OR_TWO_PI;
@@ -133,11 +145,19 @@ void or_vjp(int n, const double *x, const double *Gamma, double delta,
             gg += (w[i] * (b) + w[n + i] * (-a)) / (OR_TWO_PI * s);
         }
         if (gx) {
-            gx[k] = D[0] * w[k] + D[2] * w[n + k] + t0;
-            gx[n + k] = D[1] * w[k] + D[3] * w[n + k] + t1;
+            gx[r] = D[0] * w[k] + D[2] * w[n + k] + t0;
+            gx[nrows + r] = D[1] * w[k] + D[3] * w[n + k] + t1;
         }
-        if (gG) gG[k] = gg;
+        if (gG) gG[r] = gg;
     }
+}
+
+void or_vjp(int n, const double *x, const double *Gamma, double delta,
+            const double *w, double *gx, double *gG) {
+    int *rows = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; ++i) rows[i] = i;
+    or_vjp_rows(n, x, Gamma, delta, w, rows, n, gx, gG);
+    free(rows);
 }
 
 /* J Phi for an (2n x M) column-major basis: each column is one J v product. */

@@ -16,6 +16,7 @@ from .build_oracle import build
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 
 def _load():
@@ -27,6 +28,8 @@ def _load():
             "or_jvp": [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp],
             "or_vjp": [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp, _dp],
             "or_jphi": [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp],
+            "or_jvp_rows": [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _ip, ctypes.c_int, _dp],
+            "or_vjp_rows": [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _ip, ctypes.c_int, _dp, _dp],
         }.items():
             fn = getattr(lib, name)
             fn.argtypes = args
@@ -67,20 +70,35 @@ def velocity(x, Gamma, delta, targets=None, with_selfjac=False):
     return f
 
 
-def jvp(x, Gamma, delta, v):
-    """(d f / d x) v over all blocks."""
+def jvp(x, Gamma, delta, v, rows=None):
+    """(d f / d x) v over all blocks; with ``rows`` only those bodies' rows,
+    returned as [chi rows..., psi rows...]."""
     x, Gamma, v = _c(x), _c(Gamma), _c(v)
-    out = np.empty_like(x)
-    _load().or_jvp(Gamma.size, _p(x), _p(Gamma), float(delta), _p(v), _p(out))
+    if rows is None:
+        out = np.empty_like(x)
+        _load().or_jvp(Gamma.size, _p(x), _p(Gamma), float(delta), _p(v), _p(out))
+        return out
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.empty(2 * rows.size)
+    _load().or_jvp_rows(Gamma.size, _p(x), _p(Gamma), float(delta), _p(v),
+                        rows.ctypes.data_as(_ip), rows.size, _p(out))
     return out
 
 
-def vjp(x, Gamma, delta, w):
-    """((d f / d x)^T w, (d f / d Gamma)^T w)."""
+def vjp(x, Gamma, delta, w, rows=None):
+    """((d f / d x)^T w, (d f / d Gamma)^T w); with ``rows`` only those
+    bodies' entries ([chi..., psi...] and [Gamma...])."""
     x, Gamma, w = _c(x), _c(Gamma), _c(w)
-    gx = np.empty_like(x)
-    gG = np.empty_like(Gamma)
-    _load().or_vjp(Gamma.size, _p(x), _p(Gamma), float(delta), _p(w), _p(gx), _p(gG))
+    if rows is None:
+        gx = np.empty_like(x)
+        gG = np.empty_like(Gamma)
+        _load().or_vjp(Gamma.size, _p(x), _p(Gamma), float(delta), _p(w), _p(gx), _p(gG))
+        return gx, gG
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    gx = np.empty(2 * rows.size)
+    gG = np.empty(rows.size)
+    _load().or_vjp_rows(Gamma.size, _p(x), _p(Gamma), float(delta), _p(w),
+                        rows.ctypes.data_as(_ip), rows.size, _p(gx), _p(gG))
     return gx, gG
 
 

@@ -1,0 +1,632 @@
+// Full-order model: one implicit trapezoid step solved by Newton (Sec. 2,
+// Eq. linKstep) -- the C-ABI entry fom_step and its device kernels.
+//
+// Host-driven Newton loop; every heavy product (velocity, self blocks, J v)
+// runs in the all-pairs kernels of bs_pair.cu, every vector operation and
+// reduction in the kernels below (FP64 state, deterministic fixed-order
+// reductions: per-block partials, the last block to finish sums them in
+// block order).  Linear solves:
+//   block-diagonal : per-body 2x2 solve with (I - dt/2 D_i)
+//   JFNK           : restarted right-preconditioned GMRES with classical
+//                    Gram-Schmidt applied twice (CGS2) on the device; the
+//                    (m+1) x m Hessenberg least-squares (Givens) on the host
+//   dense          : FP64 assembly of I - dt/2 J, LU with partial pivoting in
+//                    one cooperative kernel (one grid barrier per column),
+//                    forward/back substitution in one CTA.
+#include <cooperative_groups.h>
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ptrom {
+namespace cg = cooperative_groups;
+
+constexpr int kRedThreads = 256;
+constexpr int kMaxRestart = 64;
+constexpr int kMaxDots = kMaxRestart + 2;
+constexpr int kDenseMaxN = 4096;
+
+// ---------------------------------------------------------------- reductions
+struct Red {
+    double *partials;        // [gridDim.x][nk]
+    unsigned int *counter;   // zero between launches (reset by the last block)
+    double *out;             // [nk]
+};
+
+// Sum `v` over the block; thread 0 returns the total.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    return s;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// After every block has written its nk partials: the last block sums them
+// into red.out (warp w takes k = w, w + nwarps, ...; lanes stride the blocks;
+// fixed order, so the result is deterministic) and resets the counter.
+__device__ __forceinline__ void finish_reduction(const Red &red, int nk) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(red.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < nk; k += nw) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += red.partials[(size_t)b * nk + k];
+        s = warp_sum(s);
+        if (lane == 0) red.out[k] = s;
+    }
+    if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+// r = xi - xprev - hdt (fxi + fprev);   out = {||r||^2, ||xi||^2}
+__global__ void k_residual(int n2, const double *xi, const double *xprev, const double *fxi,
+                           const double *fprev, double hdt, double *r, Red red) {
+    __shared__ double sh[32];
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+        const double v = xi[i] - xprev[i] - hdt * (fxi[i] + fprev[i]);
+        r[i] = v;
+        s0 += v * v;
+        s1 += xi[i] * xi[i];
+    }
+    double t0 = block_sum(s0, sh);
+    double t1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) {
+        red.partials[blockIdx.x * 2 + 0] = t0;
+        red.partials[blockIdx.x * 2 + 1] = t1;
+    }
+    finish_reduction(red, 2);
+}
+
+// out[k] = <V_k, w> for k < K (V: K rows of length n2); with V == nullptr,
+// out[0] = <w, w>.  One pass: each thread keeps its w entries in registers
+// (at most kMaxPer per thread), warps reduce every dot by shuffles, one CTA
+// barrier combines the warps.
+constexpr int kMaxPer = 8;
+__global__ void k_multidot(int n2, int K, const double *V, const double *w, Red red) {
+    __shared__ double sh[kRedThreads / 32][kMaxDots];
+    const int stride = gridDim.x * blockDim.x;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    double wl[kMaxPer];
+#pragma unroll
+    for (int e = 0; e < kMaxPer; ++e) {
+        const int i = i0 + e * stride;
+        wl[e] = i < n2 ? w[i] : 0.0;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < K; ++k) {
+        const double *vk = V ? V + (size_t)k * n2 : w;
+        double s = 0.0;
+#pragma unroll
+        for (int e = 0; e < kMaxPer; ++e) {
+            const int i = i0 + e * stride;
+            if (i < n2) s += vk[i] * wl[e];
+        }
+        s = warp_sum(s);
+        if (lane == 0) sh[warp][k] = s;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double s = 0.0;
+        for (int wq = 0; wq < kRedThreads / 32; ++wq) s += sh[wq][k];
+        red.partials[(size_t)blockIdx.x * K + k] = s;
+    }
+    finish_reduction(red, K);
+}
+
+// w -= sum_k h[k] V_k;  out[0] = ||w||^2
+__global__ void k_orth_update(int n2, int K, const double *V, const double *h, double *w, Red red) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+        double v = w[i];
+        for (int k = 0; k < K; ++k) v -= h[k] * V[(size_t)k * n2 + i];
+        w[i] = v;
+        s += v * v;
+    }
+    const double t = block_sum(s, sh);
+    if (threadIdx.x == 0) red.partials[blockIdx.x] = t;
+    finish_reduction(red, 1);
+}
+
+// y = alpha * x
+__global__ void k_scale(int n2, const double *x, double alpha, double *y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) y[i] = alpha * x[i];
+}
+
+// u = sum_k y[k] V_k   (y is a device array of K coefficients)
+__global__ void k_combine(int n2, int K, const double *V, const double *y, double *u) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += y[k] * V[(size_t)k * n2 + i];
+        u[i] = s;
+    }
+}
+
+// Block-diagonal solve: z_i = scale * (I - hdt D_i)^{-1} v_i, added to zacc
+// when accumulate is set.  D = [D00 | D01 | D10], D11 = -D00.
+__global__ void k_blockdiag(int n, const double *D, const double *v, double hdt, double scale,
+                            double *z, int accumulate) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d00 = D[i], d01 = D[n + i], d10 = D[2 * n + i], d11 = -d00;
+        const double m00 = 1.0 - hdt * d00, m01 = -hdt * d01, m10 = -hdt * d10, m11 = 1.0 - hdt * d11;
+        const double det = m00 * m11 - m01 * m10;
+        const double r0 = v[i], r1 = v[n + i];
+        const double z0 = scale * (m11 * r0 - m01 * r1) / det;
+        const double z1 = scale * (m00 * r1 - m10 * r0) / det;
+        if (accumulate) {
+            z[i] += z0;
+            z[n + i] += z1;
+        } else {
+            z[i] = z0;
+            z[n + i] = z1;
+        }
+    }
+}
+
+// w = z - hdt * jz
+__global__ void k_lin_op(int n2, const double *z, const double *jz, double hdt, double *w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x)
+        w[i] = z[i] - hdt * jz[i];
+}
+
+// r0 = b - (d - hdt * jd)
+__global__ void k_restart_res(int n2, const double *b, const double *d, const double *jd, double hdt,
+                              double *r0) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x)
+        r0[i] = b[i] - (d[i] - hdt * jd[i]);
+}
+
+// y += a * x
+__global__ void k_axpy(int n2, double a, const double *x, double *y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) y[i] += a * x[i];
+}
+
+// ---------------------------------------------------------------- dense path
+// M = I - hdt J (row-major m x m, m = 2n); J's diagonal blocks are the self
+// blocks D, the off-diagonal block (i, j) is -gamma_j A(x_i - x_j).
+__global__ void k_dense_assemble(int n, const double *x, const double *G, double delta, const double *D,
+                                 double hdt, double *M) {
+    const int m = 2 * n;
+    const long long total = (long long)m * m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(e / m), col = (int)(e % m);
+        const int i = row % n, ci = row / n, j = col % n, cj = col / n;
+        double Jij;
+        if (i == j) {
+            const double d00 = D[i], d01 = D[n + i], d10 = D[2 * n + i];
+            Jij = ci == 0 ? (cj == 0 ? d00 : d01) : (cj == 0 ? d10 : -d00);
+        } else {
+            const double a = x[i] - x[j], b = x[n + i] - x[n + j];
+            if (a == 0.0 && b == 0.0) {
+                Jij = 0.0;
+            } else {
+                const double s = a * a + b * b + delta, s2 = s * s;
+                double A;
+                if (ci == 0) A = cj == 0 ? 2.0 * a * b / s2 : -1.0 / s + 2.0 * b * b / s2;
+                else A = cj == 0 ? 1.0 / s - 2.0 * a * a / s2 : -2.0 * a * b / s2;
+                Jij = -(G[j] * kInv2Pi) * A;
+            }
+        }
+        M[e] = (row == col ? 1.0 : 0.0) - hdt * Jij;
+    }
+}
+
+// In-place LU with partial pivoting; rows are permuted logically (perm[l] is
+// the physical row holding logical row l).  Every CTA finds the pivot itself
+// (same data, same order -> same choice), so one grid barrier per column.
+__global__ void k_lu_coop(int m, double *A, int *perm, int *status) {
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ int sperm[];
+    __shared__ double bval[32];
+    __shared__ int bidx[32];
+    __shared__ int piv_s;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sperm[i] = i;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int gwarp = blockIdx.x * nwarps + warp, gwarps = gridDim.x * nwarps;
+    for (int k = 0; k < m; ++k) {
+        // pivot search over logical rows k..m-1 (max |a|, ties -> lowest row)
+        double best = -1.0;
+        int bi = m;
+        for (int l = k + threadIdx.x; l < m; l += blockDim.x) {
+            const double v = fabs(A[(size_t)sperm[l] * m + k]);
+            if (v > best || (v == best && l < bi)) { best = v; bi = l; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { bval[warp] = best; bidx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bb = -1.0;
+            int ii = m;
+            for (int w = 0; w < nwarps; ++w)
+                if (bval[w] > bb || (bval[w] == bb && bidx[w] < ii)) { bb = bval[w]; ii = bidx[w]; }
+            const int t = sperm[k];
+            sperm[k] = sperm[ii];
+            sperm[ii] = t;
+            piv_s = (bb > 0.0) ? 1 : 0;
+        }
+        __syncthreads();
+        if (!piv_s) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) *status = 1 + k;  // singular at column k
+            break;  // every CTA sees the same zero pivot and leaves together
+        }
+        const double *prow = A + (size_t)sperm[k] * m;
+        const double pkk = prow[k];
+        for (int l = k + 1 + gwarp; l < m; l += gwarps) {
+            double *row = A + (size_t)sperm[l] * m;
+            const double lk = row[k] / pkk;
+            for (int c = k + 1 + lane; c < m; c += 32) row[c] -= lk * prow[c];
+            __syncwarp();
+            if (lane == 0) row[k] = lk;
+        }
+        grid.sync();
+    }
+    if (blockIdx.x == 0) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = sperm[i];
+    }
+}
+
+// Solve (LU) d = rhs * scale with the factors of k_lu_coop (one CTA).
+__global__ void k_lu_solve(int m, const double *A, const int *perm, const double *rhs, double scale, double *y) {
+    for (int l = threadIdx.x; l < m; l += blockDim.x) y[l] = scale * rhs[perm[l]];
+    __syncthreads();
+    // forward: unit lower
+    for (int k = 0; k < m; ++k) {
+        const double yk = y[k];
+        for (int l = k + 1 + threadIdx.x; l < m; l += blockDim.x) y[l] -= A[(size_t)perm[l] * m + k] * yk;
+        __syncthreads();
+    }
+    // backward: upper
+    for (int k = m - 1; k >= 0; --k) {
+        if (threadIdx.x == 0) y[k] = y[k] / A[(size_t)perm[k] * m + k];
+        __syncthreads();
+        const double yk = y[k];
+        for (int l = threadIdx.x; l < k; l += blockDim.x) y[l] -= A[(size_t)perm[l] * m + k] * yk;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- workspace
+struct Work {
+    double *xprev, *fprev, *fxi, *r, *D, *d, *jz, *w, *z, *b, *V, *partials, *redout, *ydev, *M;
+    void *pack;
+    unsigned int *counter;
+    int *perm, *status;
+    size_t bytes;
+};
+
+static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+static int red_grid(int n2) {
+    int g = (n2 + kRedThreads - 1) / kRedThreads;
+    const int cap = 2 * device_sm_count();
+    g = g < 1 ? 1 : (g > cap ? cap : g);
+    // k_multidot keeps at most kMaxPer entries of w per thread
+    const int need = (n2 + kRedThreads * kMaxPer - 1) / (kRedThreads * kMaxPer);
+    return g < need ? need : g;
+}
+
+static Work layout(const ptrom_fom_params *p, int n, char *base) {
+    Work W{};
+    size_t off = 0;
+    const size_t n2 = 2 * (size_t)n;
+    auto take = [&](size_t bytes) {
+        char *ptr = base ? base + off : nullptr;
+        off += align256(bytes);
+        return ptr;
+    };
+    W.xprev = (double *)take(n2 * 8);
+    W.fprev = (double *)take(n2 * 8);
+    W.fxi = (double *)take(n2 * 8);
+    W.r = (double *)take(n2 * 8);
+    W.D = (double *)take(3 * (size_t)n * 8);
+    W.d = (double *)take(n2 * 8);
+    W.jz = (double *)take(n2 * 8);
+    W.w = (double *)take(n2 * 8);
+    W.z = (double *)take(n2 * 8);
+    W.b = (double *)take(n2 * 8);
+    const int m = (p->jac_mode == PTROM_JAC_JFNK) ? p->gmres_restart : 0;
+    W.V = (double *)take((size_t)(m + 1) * n2 * 8);
+    W.partials = (double *)take((size_t)2 * device_sm_count() * kMaxDots * 8);
+    W.redout = (double *)take(4 * kMaxDots * 8);
+    W.ydev = (double *)take(kMaxDots * 8);
+    W.counter = (unsigned int *)take(64);
+    W.pack = take(pack_scratch_bytes(n));
+    if (p->jac_mode == PTROM_JAC_DENSE) {
+        W.M = (double *)take(n2 * n2 * 8);
+        W.perm = (int *)take(n2 * 4);
+        W.status = (int *)take(64);
+    }
+    W.bytes = off;
+    return W;
+}
+
+static int validate(const ptrom_fom_params *p, int n) {
+    if (!p) return set_error(PTROM_EINVAL, "fom: NULL params");
+    if (n < 2) return set_error(PTROM_EINVAL, "fom: n must be >= 2");
+    if (!(p->dt > 0.0)) return set_error(PTROM_EINVAL, "fom: dt must be > 0");
+    if (!(p->delta >= 0.0)) return set_error(PTROM_EINVAL, "fom: delta must be >= 0");
+    if (!(p->tol >= 0.0)) return set_error(PTROM_EINVAL, "fom: tol must be >= 0");
+    if (p->max_iter < 1) return set_error(PTROM_EINVAL, "fom: max_iter must be >= 1");
+    if (p->p_it < 1) return set_error(PTROM_EINVAL, "fom: p_it must be >= 1");
+    if (p->prec != PTROM_FP32C && p->prec != PTROM_FP64) return set_error(PTROM_EINVAL, "fom: bad prec");
+    if (p->jac_mode == PTROM_JAC_JFNK) {
+        if (p->gmres_restart < 1 || p->gmres_restart > kMaxRestart)
+            return set_error(PTROM_EINVAL, "fom: gmres_restart must be in [1, %d]", kMaxRestart);
+        if (p->gmres_max_iter < 1) return set_error(PTROM_EINVAL, "fom: gmres_max_iter must be >= 1");
+        if (!(p->gmres_rtol > 0.0)) return set_error(PTROM_EINVAL, "fom: gmres_rtol must be > 0");
+    } else if (p->jac_mode == PTROM_JAC_DENSE) {
+        if (n > kDenseMaxN) return set_error(PTROM_EINVAL, "fom: dense Jacobian limited to n <= %d", kDenseMaxN);
+    } else if (p->jac_mode != PTROM_JAC_BLOCKDIAG) {
+        return set_error(PTROM_EINVAL, "fom: bad jac_mode %d", p->jac_mode);
+    }
+    return PTROM_OK;
+}
+
+// ---------------------------------------------------------------- solvers
+struct Ctx {
+    const ptrom_fom_params *p;
+    int n, n2;
+    const double *G;
+    const double *xi;
+    double hdt;
+    cudaStream_t st;
+    Work W;
+    int grid, rgrid;
+    ptrom_fom_stats *stats;
+};
+
+static Red mkred(const Work &W, int slot) { return Red{W.partials, W.counter, W.redout + slot * kMaxDots}; }
+
+static int fetch(const Ctx &c, const double *dev, double *host, int count) {
+    PTROM_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, c.st));
+    PTROM_CUDA(cudaStreamSynchronize(c.st));
+    return PTROM_OK;
+}
+
+// A y = (I - hdt J) y through the all-pairs J v kernel.
+static int apply_jvp(Ctx &c, const double *v, double *out) {
+    PTROM_TRY(jvp(c.n, c.xi, c.G, c.p->delta, v, out, c.p->prec, c.st, 0, c.W.pack));
+    if (c.stats) c.stats->jvp_evals++;
+    return PTROM_OK;
+}
+
+// Solve (I - hdt J) d = rhs_scale * rhs with right-preconditioned GMRES(m).
+static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d) {
+    const int n2 = c.n2, m = c.p->gmres_restart;
+    Work &W = c.W;
+    PTROM_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n2, c.st));
+    k_scale<<<c.grid, 256, 0, c.st>>>(n2, rhs, rhs_scale, W.b);
+    count_launch();
+    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, W.b, mkred(W, 0));
+    count_launch();
+    double bn2 = 0.0;
+    PTROM_TRY(fetch(c, W.redout, &bn2, 1));
+    const double bnorm = sqrt(bn2);
+    if (bnorm == 0.0) return PTROM_OK;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hbuf(3 * kMaxDots);
+    int total = 0;
+    const double *r0 = W.b;  // first cycle: r0 = b (d = 0)
+    double beta = bnorm;
+    while (true) {
+        k_scale<<<c.grid, 256, 0, c.st>>>(n2, r0, 1.0 / beta, W.V);
+        count_launch();
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jl = -1;
+        bool done = false;
+        for (int j = 0; j < m; ++j) {
+            double *vj = W.V + (size_t)j * n2;
+            k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, vj, c.hdt, 1.0, W.z, 0);
+            count_launch();
+            PTROM_TRY(apply_jvp(c, W.z, W.jz));
+            k_lin_op<<<c.grid, 256, 0, c.st>>>(n2, W.z, W.jz, c.hdt, W.w);
+            count_launch();
+            // CGS2
+            k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.w, mkred(W, 0));
+            count_launch();
+            k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.redout, W.w, mkred(W, 2));
+            count_launch();
+            k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.w, mkred(W, 1));
+            count_launch();
+            k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.redout + kMaxDots, W.w, mkred(W, 2));
+            count_launch();
+            PTROM_CUDA(cudaGetLastError());
+            PTROM_TRY(fetch(c, W.redout, hbuf.data(), 3 * kMaxDots));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hbuf[i] + hbuf[kMaxDots + i];
+            const double hn = sqrt(hbuf[2 * kMaxDots]);
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (!isfinite(hn)) return set_error(PTROM_ENAN, "fom: non-finite Krylov vector");
+            if (hn > 0.0) {
+                k_scale<<<c.grid, 256, 0, c.st>>>(n2, W.w, 1.0 / hn, W.V + (size_t)(j + 1) * n2);
+                count_launch();
+            }
+            // Givens
+            for (int i = 0; i < j; ++i) {
+                const double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b2;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b2;
+            }
+            const double a = H[(size_t)j * m + j], b2 = H[(size_t)(j + 1) * m + j];
+            const double rr = hypot(a, b2);
+            cs[j] = rr > 0 ? a / rr : 1.0;
+            sn[j] = rr > 0 ? b2 / rr : 0.0;
+            H[(size_t)j * m + j] = rr;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++total;
+            jl = j;
+            if (c.stats) c.stats->linear_iters++;
+            if (fabs(g[j + 1]) <= c.p->gmres_rtol * bnorm || total >= c.p->gmres_max_iter || hn == 0.0) {
+                done = true;
+                break;
+            }
+        }
+        // y = R^{-1} g, d += M^{-1} V y
+        const int K = jl + 1;
+        for (int i = K - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int k = i + 1; k < K; ++k) s -= H[(size_t)i * m + k] * y[k];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
+        }
+        PTROM_CUDA(cudaMemcpyAsync(W.ydev, y.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c.st));
+        k_combine<<<c.grid, 256, 0, c.st>>>(n2, K, W.V, W.ydev, W.w);
+        count_launch();
+        k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, W.w, c.hdt, 1.0, d, 1);
+        count_launch();
+        PTROM_CUDA(cudaGetLastError());
+        if (done) break;
+        // restart: r0 = b - A d
+        PTROM_TRY(apply_jvp(c, d, W.jz));
+        k_restart_res<<<c.grid, 256, 0, c.st>>>(n2, W.b, d, W.jz, c.hdt, W.z);
+        count_launch();
+        k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, W.z, mkred(W, 0));
+        count_launch();
+        double r2 = 0.0;
+        PTROM_TRY(fetch(c, W.redout, &r2, 1));
+        beta = sqrt(r2);
+        if (beta <= c.p->gmres_rtol * bnorm) break;
+        r0 = W.z;
+    }
+    // the last k_scale may have consumed W.z as r0; callers only read d.
+    return PTROM_OK;
+}
+
+static int dense_factor(Ctx &c) {
+    const int m = c.n2;
+    Work &W = c.W;
+    const long long total = (long long)m * m;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8 * device_sm_count()) blocks = 8 * device_sm_count();
+    k_dense_assemble<<<blocks, 256, 0, c.st>>>(c.n, c.xi, c.G, c.p->delta, W.D, c.hdt, W.M);
+    count_launch();
+    PTROM_CUDA(cudaGetLastError());
+    PTROM_CUDA(cudaMemsetAsync(W.status, 0, sizeof(int), c.st));
+    const int threads = 512;
+    const size_t smem = sizeof(int) * (size_t)m;
+    int per_sm = 0;
+    PTROM_CUDA(cudaFuncSetAttribute(k_lu_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PTROM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_coop, threads, smem));
+    if (per_sm < 1) return set_error(PTROM_ECUDA, "fom: LU kernel cannot be resident");
+    int grid = per_sm * device_sm_count();        // co-resident by construction
+    const int need = (m + threads / 32 - 1) / (threads / 32);  // one warp per row at k = 0
+    if (grid > need) grid = need;
+    int mm = m;
+    double *A = W.M;
+    int *perm = W.perm, *status = W.status;
+    void *args[] = {&mm, &A, &perm, &status};
+    PTROM_CUDA(cudaLaunchCooperativeKernel((void *)k_lu_coop, dim3(grid), dim3(threads), args, smem, c.st));
+    count_launch();
+    int st = 0;
+    PTROM_CUDA(cudaMemcpyAsync(&st, W.status, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    PTROM_CUDA(cudaStreamSynchronize(c.st));
+    if (st != 0) return set_error(PTROM_ENAN, "fom: dense Jacobian singular at column %d", st - 1);
+    return PTROM_OK;
+}
+
+}  // namespace ptrom
+
+using namespace ptrom;
+
+extern "C" size_t fom_workspace_bytes(const ptrom_fom_params *p, int n) {
+    if (validate(p, n) != PTROM_OK) return 0;
+    return layout(p, n, nullptr).bytes;
+}
+
+extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x, double *f,
+                        void *work, size_t work_bytes, ptrom_fom_stats *stats, ptrom_stream_t stream) {
+    PTROM_TRY(validate(p, n));
+    if (!Gamma || !x || !f || !work) return set_error(PTROM_EINVAL, "fom_step: NULL pointer");
+    if (((uintptr_t)work) & 255) return set_error(PTROM_EINVAL, "fom_step: work must be 256-byte aligned");
+    Ctx c{};
+    c.p = p;
+    c.n = n;
+    c.n2 = 2 * n;
+    c.G = Gamma;
+    c.xi = x;
+    c.hdt = 0.5 * p->dt;
+    c.st = (cudaStream_t)stream;
+    c.W = layout(p, n, (char *)work);
+    if (work_bytes < c.W.bytes)
+        return set_error(PTROM_EINVAL, "fom_step: work has %zu bytes, needs %zu", work_bytes, c.W.bytes);
+    c.grid = (c.n2 + 255) / 256;
+    if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
+    c.rgrid = red_grid(c.n2);
+    ptrom_fom_stats local{};
+    c.stats = stats ? stats : &local;
+    memset(c.stats, 0, sizeof(*c.stats));
+    Work &W = c.W;
+    PTROM_CUDA(cudaMemsetAsync(W.counter, 0, 64, c.st));
+    PTROM_CUDA(cudaMemcpyAsync(W.xprev, x, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
+    PTROM_CUDA(cudaMemcpyAsync(W.fprev, f, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
+    bool have_jac = false;
+    for (int k = 0; k <= p->max_iter; ++k) {
+        const bool refresh = (k % p->p_it == 0) || !have_jac;
+        PTROM_TRY(velocity(n, x, n, x, Gamma, p->delta, W.fxi, refresh ? W.D : nullptr, p->prec, c.st, 0,
+                           W.pack));
+        c.stats->velocity_evals++;
+        k_residual<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, x, W.xprev, W.fxi, W.fprev, c.hdt, W.r, mkred(W, 0));
+        count_launch();
+        PTROM_CUDA(cudaGetLastError());
+        double nr[2];
+        PTROM_TRY(fetch(c, W.redout, nr, 2));
+        const double rn = sqrt(nr[0]), xn = sqrt(nr[1]);
+        if (k == 0) c.stats->res_norm0 = rn;
+        c.stats->res_norm = rn;
+        if (!isfinite(rn)) return set_error(PTROM_ENAN, "fom_step: non-finite residual at iteration %d", k);
+        const bool conv = rn <= p->tol * (xn > 1.0 ? xn : 1.0);
+        if (conv || k == p->max_iter) {
+            PTROM_CUDA(cudaMemcpyAsync(f, W.fxi, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
+            if (!conv)
+                return set_error(PTROM_ENOCONV, "fom_step: %d Newton iterations, |r| = %.3e", k, rn);
+            return PTROM_OK;
+        }
+        c.stats->newton_iters++;
+        if (p->jac_mode == PTROM_JAC_BLOCKDIAG) {
+            k_blockdiag<<<c.grid, 256, 0, c.st>>>(n, W.D, W.r, c.hdt, -1.0, x, 1);
+            count_launch();
+        } else if (p->jac_mode == PTROM_JAC_JFNK) {
+            PTROM_TRY(gmres(c, W.r, -1.0, W.d));
+            k_axpy<<<c.grid, 256, 0, c.st>>>(c.n2, 1.0, W.d, x);
+            count_launch();
+        } else {
+            if (refresh) PTROM_TRY(dense_factor(c));
+            k_lu_solve<<<1, 1024, 0, c.st>>>(c.n2, W.M, W.perm, W.r, -1.0, W.d);
+            count_launch();
+            k_axpy<<<c.grid, 256, 0, c.st>>>(c.n2, 1.0, W.d, x);
+            count_launch();
+        }
+        PTROM_CUDA(cudaGetLastError());
+        have_jac = true;
+    }
+    return PTROM_OK;
+}

@@ -1,0 +1,19 @@
+// Internal (C++) entry points shared between translation units of libptrom.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ptrom {
+
+// All-pairs launches (bs_pair.cu).  split = 0 -> automatic cluster split.
+// scratch: device buffer of at least pack_scratch_bytes(ns) bytes for the
+// packed sources, or nullptr (stream-ordered allocation from the pool).
+int velocity(int nt, const double *xt, int ns, const double *xs, const double *G, double delta,
+             double *f, double *D, int prec, cudaStream_t st, int split, void *scratch = nullptr);
+int jvp(int n, const double *x, const double *G, double delta, const double *v, double *jv,
+        int prec, cudaStream_t st, int split, void *scratch = nullptr);
+int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
+        double *gG, int prec, cudaStream_t st, int split, void *scratch = nullptr);
+size_t pack_scratch_bytes(int ns);
+
+}  // namespace ptrom

@@ -1,0 +1,218 @@
+"""Thin Python binding of libptrom.so (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors must be CUDA float64 tensors on the current device; outputs
+are allocated with torch (device memory) unless passed in.  Calls are
+enqueued on torch's current CUDA stream unless ``stream`` is given.
+
+The library is loaded on import and a missing or unloadable library raises
+immediately: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libptrom.so")
+
+FP32C = 0
+FP64 = 1
+_PREC = {"fp32c": FP32C, "fp64": FP64, FP32C: FP32C, FP64: FP64}
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+
+class PtromError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ptrom status {status}: {msg}")
+        self.status = status
+
+
+JAC_BLOCKDIAG = 0
+JAC_DENSE = 1
+JAC_JFNK = 2
+_JAC = {"blockdiag": JAC_BLOCKDIAG, "dense": JAC_DENSE, "jfnk": JAC_JFNK}
+
+# status codes (include/ptrom.h)
+OK, EINVAL, ECUDA, ENOCONV, ENAN, ETIMEOUT, ENOMEM = 0, -1, -2, -3, -4, -5, -6
+
+
+class FomParams(ctypes.Structure):
+    """Mirror of ptrom_fom_params."""
+    _fields_ = [("dt", _d), ("delta", _d), ("tol", _d), ("max_iter", _i), ("jac_mode", _i),
+                ("p_it", _i), ("prec", _i), ("gmres_restart", _i), ("gmres_max_iter", _i),
+                ("gmres_rtol", _d)]
+
+
+class FomStats(ctypes.Structure):
+    """Mirror of ptrom_fom_stats."""
+    _fields_ = [("newton_iters", _i), ("linear_iters", _i), ("velocity_evals", _i),
+                ("jvp_evals", _i), ("res_norm", _d), ("res_norm0", _d)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def fom_params(dt, delta, mode="blockdiag", tol=None, max_iter=100, p_it=None, prec="fp32c",
+               gmres_restart=30, gmres_max_iter=200, gmres_rtol=1e-4):
+    """Build a FomParams; tol defaults to 1e-12 (FP64) or 1e-8 (FP32C).
+
+    p_it defaults to 1 (refresh every Newton iteration) for the dense and
+    block-diagonal Jacobians; for JFNK the self blocks only precondition GMRES
+    (the Krylov products use the exact J at the current iterate), so they are
+    refreshed once per time step (p_it = max_iter)."""
+    if p_it is None:
+        p_it = max_iter if mode == "jfnk" else 1
+    if tol is None:
+        tol = 1e-12 if _prec(prec) == FP64 else 1e-8
+    return FomParams(float(dt), float(delta), float(tol), int(max_iter), _JAC[mode], int(p_it),
+                     _prec(prec), int(gmres_restart), int(gmres_max_iter), float(gmres_rtol))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "ptrom_last_error": ([ctypes.c_char_p, ctypes.c_size_t], _i),
+        "ptrom_version": ([], _i),
+        "ptrom_set_source_split": ([_i], _i),
+        "bs_velocity": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
+        "bs_jvp": ([_i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
+        "bs_vjp": ([_i, _vp, _vp, _d, _vp, _vp, _vp, _i, _vp], _i),
+        "ptrom_launch_count": ([], ctypes.c_longlong),
+        "ptrom_timing_enable": ([_i], _i),
+        "ptrom_timing_read": ([ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i], _i),
+        "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
+        "fom_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                      ctypes.POINTER(FomStats), _vp], _i),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib.ptrom_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def _check(status):
+    if status != 0:
+        raise PtromError(status, last_error())
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prec(p):
+    try:
+        return _PREC[p]
+    except KeyError:
+        raise ValueError(f"prec must be 'fp32c' or 'fp64', got {p!r}") from None
+
+
+KERNEL_KINDS = ["velocity", "velocity_selfjac", "jvp", "vjp", "jphi", "ptrom_step"]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far (process-wide)."""
+    return int(lib.ptrom_launch_count())
+
+
+def timing_enable(on: bool) -> None:
+    lib.ptrom_timing_enable(1 if on else 0)
+
+
+def timing_read() -> dict:
+    """{kind: (total_ms, launches)} of the event-timed launches since the last read."""
+    k = len(KERNEL_KINDS)
+    ms = (_d * k)()
+    cnt = (ctypes.c_longlong * k)()
+    _check(lib.ptrom_timing_read(ms, cnt, k))
+    return {name: (ms[i], int(cnt[i])) for i, name in enumerate(KERNEL_KINDS)}
+
+
+def set_source_split(S: int) -> None:
+    """Force the all-pairs kernels' cluster source split (0 = automatic)."""
+    _check(lib.ptrom_set_source_split(int(S)))
+
+
+def bs_velocity(xs, Gamma, delta, xt=None, f_out=None, selfjac=False, prec="fp32c", stream=None):
+    """f (2 nt) at targets xt (default: the sources themselves); with
+    ``selfjac`` also the (3, nt) self blocks (D00, D01, D10)."""
+    ns = Gamma.numel()
+    xt = xs if xt is None else xt
+    nt = xt.numel() // 2
+    if f_out is None:
+        f_out = torch.empty(2 * nt, dtype=torch.float64, device=xs.device)
+    D = torch.empty(3 * nt, dtype=torch.float64, device=xs.device) if selfjac else None
+    _check(lib.bs_velocity(nt, _ptr(xt), ns, _ptr(xs), _ptr(Gamma), float(delta), _ptr(f_out),
+                           _ptr(D), _prec(prec), _stream(stream)))
+    return (f_out, D.view(3, nt)) if selfjac else f_out
+
+
+def bs_jvp(x, Gamma, delta, v, out=None, prec="fp32c", stream=None):
+    n = Gamma.numel()
+    out = torch.empty_like(x) if out is None else out
+    _check(lib.bs_jvp(n, _ptr(x), _ptr(Gamma), float(delta), _ptr(v), _ptr(out), _prec(prec),
+                      _stream(stream)))
+    return out
+
+
+def bs_vjp(x, Gamma, delta, w, want_x=True, want_gamma=True, prec="fp32c", stream=None):
+    n = Gamma.numel()
+    gx = torch.empty_like(x) if want_x else None
+    gG = torch.empty_like(Gamma) if want_gamma else None
+    _check(lib.bs_vjp(n, _ptr(x), _ptr(Gamma), float(delta), _ptr(w), _ptr(gx), _ptr(gG),
+                      _prec(prec), _stream(stream)))
+    return gx, gG
+
+
+def fom_workspace(params, n, device="cuda"):
+    nbytes = lib.fom_workspace_bytes(ctypes.byref(params), int(n))
+    if nbytes == 0:
+        raise PtromError(EINVAL, last_error())
+    return torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+
+
+def fom_step(params, Gamma, x, f, work=None, stream=None, allow_noconv=False):
+    """One implicit trapezoid step in place on (x, f).  Returns the stats dict."""
+    n = Gamma.numel()
+    if work is None:
+        work = fom_workspace(params, n, x.device)
+    st = FomStats()
+    status = lib.fom_step(ctypes.byref(params), n, _ptr(Gamma), _ptr(x), _ptr(f),
+                          ctypes.c_void_p(work.data_ptr()), work.numel(), ctypes.byref(st),
+                          _stream(stream))
+    if status == ENOCONV and allow_noconv:
+        d = st.as_dict()
+        d["converged"] = False
+        return d
+    _check(status)
+    d = st.as_dict()
+    d["converged"] = True
+    return d

@@ -1,0 +1,52 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares (CPU only).
+
+Also checks argument validation that happens before any CUDA call."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "sizeof", "return"):
+                names.add(name)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from __graft_entry__ import build_library
+    build_library()
+    from paper_2103_01983_gb300 import ptrom
+    return ptrom
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"bs_velocity", "bs_jvp", "bs_vjp", "ptrom_last_error"} <= names
+    missing = [n for n in sorted(names) if not hasattr(lib.lib, n)]
+    assert not missing, missing
+
+
+def test_invalid_arguments_rejected_before_any_cuda_call(lib):
+    L = lib.lib
+    null = ctypes.c_void_p(0)
+    assert L.bs_velocity(0, null, 10, null, null, 0.1, null, null, 0, null) == -1
+    assert "sizes" in lib.last_error()
+    assert L.bs_velocity(4, null, 4, null, null, -1.0, null, null, 0, null) == -1
+    assert L.bs_velocity(4, null, 4, null, null, 0.1, null, null, 7, null) == -1
+    assert L.bs_velocity(4, null, 4, null, null, 0.1, null, null, 0, null) == -1   # NULL arrays
+    assert L.bs_jvp(1, null, null, 0.1, null, null, 0, null) == -1
+    assert L.bs_vjp(1, null, null, 0.1, null, null, null, 0, null) == -1
+    assert L.ptrom_set_source_split(9) == -1
+    assert L.ptrom_set_source_split(0) == 0

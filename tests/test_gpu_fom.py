@@ -1,0 +1,127 @@
+"""Parity of the CUDA implicit trapezoid FOM step with the FP64 oracle (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import direct, fom, qoi
+from paper_2103_01983_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2103_01983_gb300 import ptrom
+    return ptrom
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _gpu_rollout(P, x0, G, params, steps, prec):
+    x = _dev(x0)
+    Gt = _dev(G)
+    f = P.bs_velocity(x, Gt, params.delta, prec=prec)
+    work = P.fom_workspace(params, G.size)
+    traj = [x0.copy()]
+    stats = []
+    for _ in range(steps):
+        stats.append(P.fom_step(params, Gt, x, f, work=work))
+        traj.append(x.cpu().numpy())
+    return np.array(traj), stats, f.cpu().numpy()
+
+
+def test_small_dense_fp64_matches_oracle_100_steps(P):
+    """N=256 disk, delta=0.05, dt=0.01, 100 steps, dense Newton, FP64."""
+    x0, G = W.disk(256, seed=0)
+    params = P.fom_params(0.01, 0.05, "dense", tol=1e-12, prec="fp64")
+    traj, stats, f = _gpu_rollout(P, x0, G, params, 100, "fp64")
+    ref, iters = fom.rollout(x0, G, 0.05, 0.01, 100, mode="dense", tol=1e-12)
+    err = np.abs(traj - ref).max()
+    assert err <= 1e-10, err
+    assert all(s["converged"] for s in stats)
+    np.testing.assert_allclose(f, direct.velocity(traj[-1], G, 0.05), atol=1e-11)
+    # linear impulse to Newton tolerance
+    P0 = qoi.linear_impulse(x0, G)
+    assert np.abs(qoi.linear_impulse(traj[-1], G) - P0).max() <= 1e-9
+
+
+@pytest.mark.parametrize("mode", ["blockdiag", "jfnk", "dense"])
+def test_modes_fp64_against_oracle(P, mode):
+    x0, G = W.disk(300, seed=3)
+    params = P.fom_params(0.01, 0.05, mode, tol=1e-13, prec="fp64", gmres_rtol=1e-10)
+    traj, stats, _ = _gpu_rollout(P, x0, G, params, 4, "fp64")
+    ref, _ = fom.rollout(x0, G, 0.05, 0.01, 4, mode="dense", tol=1e-14)
+    assert np.abs(traj - ref).max() <= 1e-11
+
+
+def test_jfnk_fp32c_against_oracle(P):
+    """Two-cluster N=2048: JFNK with FP32 pair sums vs the FP64 dense oracle."""
+    x0, G = W.two_cluster(2048, seed=0)
+    params = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c")
+    traj, stats, _ = _gpu_rollout(P, x0, G, params, 5, "fp32c")
+    ref, _ = fom.rollout(x0, G, 0.02, 0.005, 5, mode="jfnk", tol=1e-13, gmres_tol=1e-12)
+    rel = np.linalg.norm(traj[-1] - ref[-1]) / np.linalg.norm(ref[-1] - x0)
+    assert rel <= 1e-5, rel
+    assert all(s["converged"] for s in stats)
+    assert all(s["linear_iters"] > 0 for s in stats)
+
+
+def test_two_vortex_rotation_on_gpu(P):
+    d, delta, dt = 0.8, 0.05, 0.1
+    x0, G = W.two_vortex(d, 1.0, 1.0)
+    params = P.fom_params(dt, delta, "dense", tol=1e-14, prec="fp64")
+    traj, _, _ = _gpu_rollout(P, x0, G, params, 10, "fp64")
+    omega = 2.0 / (2 * np.pi * (d * d + delta))
+    ang = np.unwrap(np.arctan2(traj[:, 3] - traj[:, 2], traj[:, 1] - traj[:, 0]))
+    np.testing.assert_allclose(np.diff(ang), 2 * np.arctan(omega * dt / 2), rtol=1e-11)
+
+
+def test_noconv_and_bad_params(P):
+    x0, G = W.disk(64, seed=5)
+    params = P.fom_params(0.01, 0.05, "blockdiag", tol=0.0, max_iter=2, prec="fp64")
+    x, Gt = _dev(x0), _dev(G)
+    f = P.bs_velocity(x, Gt, 0.05, prec="fp64")
+    st = P.fom_step(params, Gt, x, f, allow_noconv=True)
+    assert not st["converged"] and st["newton_iters"] == 2
+    with pytest.raises(P.PtromError) as e:
+        P.fom_step(params, Gt, x, f)
+    assert e.value.status == P.ENOCONV
+    bad = P.fom_params(-1.0, 0.05, "blockdiag")
+    with pytest.raises(P.PtromError):
+        P.fom_workspace(bad, 64)
+    # NaN-seeded state -> ENAN, never a hang
+    xn = x.clone()
+    xn[3] = float("nan")
+    good = P.fom_params(0.01, 0.05, "blockdiag", prec="fp64")
+    with pytest.raises(P.PtromError) as e:
+        P.fom_step(good, Gt, xn, f.clone())
+    assert e.value.status == P.ENAN
+
+
+def test_full_size_step_residual_sampled(P):
+    """N=16384 two clusters, JFNK with FP32C pair sums (the benchmarked step):
+    the oracle's FP64 trapezoid residual at 256 sampled bodies is at the level
+    the FP32 velocity error allows, and the linear impulse is kept."""
+    n, delta, dt = 16384, 0.02, 0.005
+    x0, G = W.two_cluster(n, seed=0)
+    params = P.fom_params(dt, delta, "jfnk", prec="fp32c")
+    x, Gt = _dev(x0), _dev(G)
+    f = P.bs_velocity(x, Gt, delta)
+    work = P.fom_workspace(params, n)
+    rows = np.random.default_rng(40).choice(n, 256, replace=False)
+    idx = np.r_[rows, n + rows]
+    xp = x0.copy()
+    for step in range(3):
+        st = P.fom_step(params, Gt, x, f, work=work)
+        xn = x.cpu().numpy()
+        fo_new = direct.velocity(xn, G, delta, targets=xn[idx])
+        fo_old = direct.velocity(xp, G, delta, targets=xp[idx])
+        r = xn[idx] - xp[idx] - 0.5 * dt * (fo_new + fo_old)
+        step_size = np.linalg.norm(xn[idx] - xp[idx])
+        assert np.linalg.norm(r) <= 1e-5 * step_size, (step, np.linalg.norm(r), step_size)
+        rel_f = np.linalg.norm(f.cpu().numpy()[idx] - fo_new) / np.linalg.norm(fo_new)
+        assert rel_f <= 1e-5
+        np.testing.assert_allclose(qoi.linear_impulse(xn, G), qoi.linear_impulse(x0, G), atol=1e-9)
+        xp = xn
