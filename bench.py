@@ -269,7 +269,7 @@ def run_ours(args):
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     dom_ms, dom_cnt = ktimes[dom]
     achieved = FLOPS_PER_PAIR[dom] * n * n * dom_cnt / (dom_ms * 1e-3) / 1e12 if dom_cnt else None
-    traffic = _traffic(dom)
+    traffic = _traffic(dom, n)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_src}: {sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
@@ -300,13 +300,22 @@ def run_ours(args):
     return line if rank == 0 else None
 
 
-def _traffic(kind):
-    """DRAM bytes per launch from the committed ncu summary, when it exists."""
+def _traffic(kind, n):
+    """DRAM bytes per launch from the committed ncu capture of this kernel at
+    this size; None when there is none or the kernel sources changed since."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
-            return json.load(fh).get(kind)
-    except (OSError, ValueError):
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            with open(os.path.join(ROOT, f), "rb") as src:
+                h.update(src.read())
+        if h.hexdigest() != rec["source_sha256"] or rec["sizes"].get(kind) != n:
+            return None
+        return rec.get(kind)
+    except (OSError, ValueError, KeyError):
         return None
 
 
