@@ -102,6 +102,33 @@ int bs_velocity(int nt, const double *xt, int ns, const double *xs,
                 double *selfjac_out, int prec, ptrom_stream_t stream);
 
 /*
+ * bs_velocity_noalloc -- bs_velocity for callers that must not allocate device
+ * memory while they run.  The paper has no counterpart; this is a library
+ * service.  bs_velocity takes a scratch buffer for its packed sources from a
+ * stream-ordered memory pool on every call; a control or serving loop whose
+ * memory policy forbids device allocation after start-up (an allocation can
+ * block, fail under memory pressure or change the footprint mid-run), or a
+ * process whose device memory belongs to another framework's allocator, cannot
+ * accept that.  This variant keeps the scratch in one fixed device array
+ * inside the library instead: PTROM_NOALLOC_MAX_SOURCES sources (3 MiB), held
+ * by every GPU that loads the library until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ * Arguments, outputs and precision are those of bs_velocity.
+ * Errors: as bs_velocity, plus PTROM_EINVAL when ns > PTROM_NOALLOC_MAX_SOURCES.
+ * Notes: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (every record a call reads is rewritten by that call first,
+ * so nothing needs clearing); calls that overlap on the GPU -- on different
+ * streams, or from different host threads -- race on it and must be ordered
+ * by the caller.
+ */
+#define PTROM_NOALLOC_MAX_SOURCES 65536
+int bs_velocity_noalloc(int nt, const double *xt, int ns, const double *xs,
+                        const double *Gamma, double delta, double *f_out,
+                        double *selfjac_out, int prec, ptrom_stream_t stream);
+
+/*
  * bs_jvp -- Jacobian-vector product of the kernel, jv = (d f / d x) v, with
  * all blocks (the exact Jacobian whose product the Gauss-Newton/LSPG step of
  * Sec. 3.2 and a Jacobian-free Newton solve of Eq. linKstep need):

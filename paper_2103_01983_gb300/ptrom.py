@@ -84,6 +84,7 @@ def _load():
         "ptrom_version": ([], _i),
         "ptrom_set_source_split": ([_i], _i),
         "bs_velocity": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
+        "bs_velocity_noalloc": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_jvp": ([_i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_vjp": ([_i, _vp, _vp, _d, _vp, _vp, _vp, _i, _vp], _i),
         "ptrom_launch_count": ([], ctypes.c_longlong),
@@ -173,6 +174,21 @@ def bs_velocity(xs, Gamma, delta, xt=None, f_out=None, selfjac=False, prec="fp32
     _check(lib.bs_velocity(nt, _ptr(xt), ns, _ptr(xs), _ptr(Gamma), float(delta), _ptr(f_out),
                            _ptr(D), _prec(prec), _stream(stream)))
     return (f_out, D.view(3, nt)) if selfjac else f_out
+
+
+NOALLOC_MAX_SOURCES = 65536
+
+
+def bs_velocity_noalloc(xs, Gamma, delta, f_out, xt=None, selfjac_out=None, prec="fp32c", stream=None):
+    """bs_velocity without any device allocation inside the library (its
+    scratch is a fixed array of NOALLOC_MAX_SOURCES sources); outputs must be
+    passed in.  Calls that overlap on the GPU share that scratch and race."""
+    ns = Gamma.numel()
+    xt = xs if xt is None else xt
+    nt = xt.numel() // 2
+    _check(lib.bs_velocity_noalloc(nt, _ptr(xt), ns, _ptr(xs), _ptr(Gamma), float(delta), _ptr(f_out),
+                                   _ptr(selfjac_out), _prec(prec), _stream(stream)))
+    return f_out
 
 
 def bs_jvp(x, Gamma, delta, v, out=None, prec="fp32c", stream=None):
