@@ -1,0 +1,156 @@
+"""Pins of the oracle's PTROM pieces (CPU only): POD, quadtree, ClusterPOD,
+HyperPair, greedy sampling, gappy operator, and PTROM exactness."""
+import numpy as np
+import pytest
+
+from oracle import direct, fom, rom
+from paper_2103_01983_gb300 import workloads as W
+
+
+def test_pod_properties():
+    """Orthonormal columns, descending values, the Gram matrix's leading
+    eigenpairs, and the projection error equals the discarded energy
+    (Eckart-Young), on a matrix with a known spectrum."""
+    rng = np.random.default_rng(1)
+    Q1, _ = np.linalg.qr(rng.standard_normal((60, 12)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((20, 12)))
+    true = 2.0 ** -np.arange(12)
+    S = Q1 @ np.diag(true) @ Q2.T
+    Phi, sig = rom.pod(S, 6)
+    np.testing.assert_allclose(Phi.T @ Phi, np.eye(6), atol=1e-12)
+    np.testing.assert_allclose(sig, true[:6], rtol=1e-12)
+    np.testing.assert_allclose(Phi @ Phi.T, Q1[:, :6] @ Q1[:, :6].T, atol=1e-12)
+    # Phi spans the leading eigenvectors of S S^T
+    np.testing.assert_allclose((S @ S.T) @ Phi, Phi * sig**2, atol=1e-12)
+    err = np.linalg.norm(S - Phi @ (Phi.T @ S)) ** 2
+    np.testing.assert_allclose(err, np.sum(true[6:] ** 2), rtol=1e-10)
+    # sign convention: largest-magnitude entry of each column is positive
+    assert np.all(Phi[np.argmax(np.abs(Phi), axis=0), np.arange(6)] > 0)
+
+
+def test_quadtree_structure():
+    rng = np.random.default_rng(2)
+    P = rng.uniform(-1, 1, (300, 2))
+    t = rom.QuadTree(P)
+    leaves = [nd for nd in t.nodes if nd.is_leaf]
+    counts = np.zeros(300, int)
+    for nd in leaves:
+        assert len(nd.members) == 1
+        counts[nd.members] += 1
+    assert np.all(counts == 1)
+    for nd in t.nodes:
+        for m in nd.members:
+            x, y = P[m]
+            assert nd.box[0] <= x <= nd.box[1] and nd.box[2] <= y <= nd.box[3]
+        if nd.children:
+            assert sorted(sum((c.members for c in nd.children), [])) == sorted(nd.members)
+            for c in nd.children:
+                assert c.width == pytest.approx(nd.width / 2)
+
+
+def _setup(n=120, M=4, seed=3):
+    x0, G = W.disk(n, seed=seed)
+    traj, _ = fom.rollout(x0, G, 0.05, 0.01, 12, mode="dense", tol=1e-13)
+    S = (traj[1:] - x0).T
+    Phi, sig = rom.pod(S, M)
+    return x0, G, Phi, sig
+
+
+@pytest.mark.parametrize("criterion,param", [("bh", 0.5), ("bh", 1.0), ("nb", 1.0), ("nb", 0.0)])
+def test_clusters_partition_every_target(criterion, param):
+    """For each target, its clusters' members are all other bodies, once each;
+    each cluster's Gamma~ is the brute-force member sum; x0_QT + Phi~ xhat is
+    the |Gamma|-weighted centroid of the members' reduced positions."""
+    x0, G, Phi, sig = _setup()
+    N = G.size
+    kw = {"theta": param} if criterion == "bh" else {"p_c": param}
+    cl, tree = rom.cluster_tables(Phi, sig, x0, G, np.arange(N), criterion=criterion, **kw)
+    for i, li in enumerate(cl.lists):
+        mem = sorted(sum((cl.members[c] for c in li), []))
+        assert mem == [j for j in range(N) if j != i]
+    for c, m in enumerate(cl.members):
+        assert cl.Gt[c] == pytest.approx(G[m].sum(), abs=1e-15)
+    xhat = np.random.default_rng(4).standard_normal(Phi.shape[1])
+    xq = cl.x0t + cl.Phit @ xhat
+    x = x0 + Phi @ xhat
+    Nc = len(cl.members)
+    for c, m in enumerate(cl.members):
+        w = np.abs(G[m])
+        np.testing.assert_allclose(xq[c], np.dot(w, x[m]) / w.sum(), atol=1e-13)
+        np.testing.assert_allclose(xq[Nc + c], np.dot(w, x[N + np.array(m)]) / w.sum(), atol=1e-13)
+    if criterion == "bh":
+        # every pruned node satisfies the opening criterion for its target, and
+        # none of its ancestors did (the traversal stops at the first)
+        W_ = Phi @ sig
+        pts = np.stack([W_[:N], W_[N:]], axis=1)
+        parent = {c.id: nd.id for nd in tree.nodes for c in nd.children}
+        for i, pr in enumerate(cl.pruned):
+            for nid in pr:
+                nd = tree.nodes[nid]
+                w = np.abs(G[nd.members])
+                cen = (w[:, None] * pts[nd.members]).sum(0) / w.sum()
+                assert i not in nd.members
+                assert nd.width / np.linalg.norm(cen - pts[i]) <= param + 1e-12
+                a = parent.get(nid)
+                while a is not None:
+                    an = tree.nodes[a]
+                    wa = np.abs(G[an.members])
+                    ca = (wa[:, None] * pts[an.members]).sum(0) / wa.sum()
+                    d = np.linalg.norm(ca - pts[i])
+                    assert i in an.members or d == 0 or an.width / d > param
+                    a = parent.get(a)
+        assert np.mean([len(li) for li in cl.lists]) < N - 1   # something was clustered
+
+
+def test_hyperpair_without_clustering_is_the_fom_velocity():
+    """theta = 0 never prunes: HyperPair equals Eq. 2 at x = x0 + Phi xhat."""
+    x0, G, Phi, sig = _setup()
+    N = G.size
+    cl, _ = rom.cluster_tables(Phi, sig, x0, G, np.arange(N), criterion="bh", theta=0.0)
+    assert all(len(li) == N - 1 for li in cl.lists)
+    xhat = np.random.default_rng(5).standard_normal(Phi.shape[1]) * 0.1
+    Phi_t, x0_t = rom.target_rows(Phi, x0, cl.targets)
+    f, D = rom.hyperpair(xhat, cl, Phi_t, x0_t, 0.05)
+    x = x0 + Phi @ xhat
+    fo, Do = direct.velocity(x, G, 0.05, with_selfjac=True)
+    np.testing.assert_allclose(f, fo, atol=1e-13)
+    np.testing.assert_allclose(D, Do, atol=1e-12)
+
+
+def test_greedy_sampling_small_case():
+    rng = np.random.default_rng(6)
+    N, Mr = 30, 4
+    Phi_r, _ = np.linalg.qr(rng.standard_normal((2 * N, Mr)))
+    s = rom.greedy_sample(Phi_r, 6, N)
+    assert len(s) == 6 and len(set(s)) == 6
+    np.testing.assert_array_equal(s, rom.greedy_sample(Phi_r, 6, N))
+    # n_c = min(4, 12) = 4, n_it = 4: iteration 1 takes n_a1 = 2 bodies by the
+    # energy of the first basis column alone
+    e1 = Phi_r[:N, 0] ** 2 + Phi_r[N:, 0] ** 2
+    assert list(s[:2]) == list(np.argsort(-e1, kind="stable")[:2])
+    A = rom.gappy_operator(Phi_r, s, N)
+    dofs = np.concatenate([s, N + s])
+    np.testing.assert_allclose(A @ Phi_r[dofs], np.eye(Mr), atol=1e-12)
+
+
+def test_ptrom_reproduces_fom_when_basis_spans_trajectory():
+    """M = rank of the snapshot offsets, every body sampled, no clustering:
+    the PTROM trajectory is the FOM trajectory (Gauss-Newton tolerance)."""
+    n, steps, dt, delta = 40, 10, 0.01, 0.05
+    x0, G = W.disk(n, seed=7)
+    traj, _ = fom.rollout(x0, G, delta, dt, steps, mode="dense", tol=1e-14)
+    S = (traj[1:] - x0).T
+    sv = np.linalg.svd(S, compute_uv=False)
+    M = int(np.sum(sv > 1e-12 * sv[0]))       # numerical rank (<= steps)
+    Phi, sig = rom.pod(S, M)
+    cl, _ = rom.cluster_tables(Phi, sig, x0, G, np.arange(n), criterion="bh", theta=0.0)
+    red2, snaps = rom.lspg_tier2(cl, Phi, x0, delta, dt, steps, tol=1e-12)
+    U, s, _ = np.linalg.svd(snaps, full_matrices=False)
+    Mr = int(np.sum(s > 1e-10 * s[0]))
+    Phi_r = U[:, :Mr]
+    A = rom.gappy_operator(Phi_r, np.arange(n), n)
+    red3, iters = rom.ptrom_online(cl, Phi, x0, A, delta, dt, steps, tol=1e-12)
+    rec = np.array([rom.reconstruct(z, Phi, x0) for z in red3])
+    assert np.abs(rec - traj).max() <= 1e-9
+    rec2 = np.array([rom.reconstruct(z, Phi, x0) for z in red2])
+    assert np.abs(rec2 - traj).max() <= 1e-9
