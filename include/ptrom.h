@@ -212,6 +212,82 @@ int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x,
              double *f, void *work, size_t work_bytes, ptrom_fom_stats *stats,
              ptrom_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Projection-tree ROM (PTROM): online Gauss-Newton (Alg. 4) over the hyper-
+ * reduced pairwise interaction (Alg. 5), at the sampled bodies against the
+ * clustered sources (Sec. 5.2).
+ *
+ * A model holds, for n_s sampled bodies (n_d = 2 n_s dofs, order
+ * [chi_1..chi_ns, psi_1..psi_ns]), M POD modes, M_r residual modes and N_c
+ * source clusters:
+ *   phi_s   [n_d x M]   row-major: the sampled rows of Phi (Phi bar)
+ *   x0_s    [n_d]       sampled rows of x^0(mu)
+ *   phi_c   [2 N_c x M] row-major: cluster POD surrogates Phi~ (rows
+ *                       [chi of every cluster; psi of every cluster])
+ *   x0_c    [2 N_c]     cluster reference positions x^0_QT(mu)
+ *   gamma_c [N_c]       cluster circulations Gamma~(mu)
+ *   off     [n_s + 1], idx [off[n_s]]: CSR lists, sampled body i interacts
+ *                       with clusters idx[off[i] .. off[i+1])
+ *   A       [M_r x n_d] row-major: the gappy operator [P Phi_r]^+
+ * Limits: M <= 64, M_r <= 128, n_s <= 512, N_c <= 8192 (shared-memory
+ * resident per instance).
+ * ------------------------------------------------------------------------ */
+typedef struct ptrom_model ptrom_model;
+
+typedef struct ptrom_model_desc {
+    int n_s, M, M_r, N_c;
+    double dt, delta;
+    double tol;     /* Gauss-Newton tolerance on eps (Alg. 4)               */
+    int max_gn;     /* Gauss-Newton iteration cap (the paper uses 100)      */
+    int qr_prec;    /* PTROM_FP64 (FP64 Householder QR) or PTROM_FP32C (FP32) */
+    /* HOST arrays, copied into the model */
+    const double *phi_s, *x0_s, *phi_c, *x0_c, *gamma_c, *A;
+    const int *off, *idx;
+} ptrom_model_desc;
+
+typedef struct ptrom_stats {
+    long long gn_iters;   /* Gauss-Newton iterations over all steps/instances */
+    long long steps;      /* time steps taken (all instances)                */
+    int noconv;           /* steps that hit max_gn                           */
+    int max_iters;        /* largest iteration count of one step             */
+} ptrom_stats;
+
+/* Create a model on the current device from host arrays (copied).  The
+ * model is immutable afterwards except through ptrom_set_param.
+ * Errors: sizes out of the limits, NULL arrays, CSR indices out of range. */
+int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **out);
+void ptrom_free(ptrom_model *m);
+
+/* Replace the parameter-dependent arrays (Sec. 5.2: reload the clustered
+ * circulation for a new mu) -- x0_s, phi_c, x0_c, gamma_c (HOST, same sizes;
+ * any may be NULL to keep the current one). */
+int ptrom_set_param(ptrom_model *m, const double *x0_s, const double *phi_c,
+                    const double *x0_c, const double *gamma_c);
+
+/* Device bytes of per-instance online state for a model (xhat, the carried
+ * velocity at the sampled dofs, flags). */
+size_t ptrom_state_bytes(const ptrom_model *m);
+
+/*
+ * ptrom_step -- advance `batch` independent instances of one or more models
+ * by `nsteps` time steps in ONE launch (one CTA per instance).
+ *   models  [batch] host array of model handles (may repeat one model)
+ *   state   [batch] host array of device pointers, each ptrom_state_bytes
+ *           bytes, 256-byte aligned; zero-filled state means xhat = 0 and
+ *           "carried velocity not yet computed" (computed at xhat as R11)
+ *   xhat    [batch] host array of device pointers to M doubles: on return
+ *           the reduced coordinates after the last step (also in the state)
+ *   hist    optional [batch] host array of device pointers to nsteps x M
+ *           doubles receiving xhat after every step (NULL to skip)
+ *   stats   optional host pointer; filling it synchronises the stream.
+ * Errors: PTROM_EINVAL for bad arguments.  Non-convergence of one step is
+ * counted in stats (the step keeps its last iterate, as Alg. 4 does at
+ * k = max_gn), not an error.
+ */
+int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
+               double *const *xhat, double *const *hist, int nsteps,
+               ptrom_stats *stats, ptrom_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

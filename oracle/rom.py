@@ -41,8 +41,12 @@ Readings where the paper is silent or garbled (each used by the CUDA path too):
   R8 x^QT = x^0_QT + Phi~ xhat and x^GP = x^0 + Phi xhat with the total xhat
      (Alg. 5's "Delta xhat" notation is read as the current coordinates).
   R9 Gauss-Newton runs while eps > tol (Alg. 4 prints "<"), at most 100
-     iterations; eps = ||C^T r|| / ||C_1^T r_1|| with C_1, r_1 at the step's
-     first iterate; the update is applied before eps is tested (Alg. 4 order).
+     iterations; the update is applied before eps is tested (Alg. 4 order).
+     eps is the gradient of the objective being minimised relative to its
+     value at the step's first iterate: ||C^T r|| for LSPG (Tier II, as
+     printed) and ||(A C)^T (A r)|| for the hyper-reduced problem (Tier III).
+     Alg. 4 prints the unweighted ||Phi^T J^T r||, which does not vanish at
+     the minimiser of ||A r|| when M_r > M, so that test could never be met.
   R10 A = [P Phi_r]^+ multiplies both C and D (Alg. 4 as printed).
   R11 f~^0 is HyperPair's velocity at xhat = 0; the velocity carried to the
       next step is the last one HyperPair computed in the step (Alg. 5 stores
@@ -374,8 +378,9 @@ def ptrom_online(cl: Clusters, Phi, x0, A, delta, dt, steps, tol=1e-4, max_gn=10
             f, D = hyperpair(xhat, cl, Phi_t, x0_t, delta)
             r = Phi_t @ (xhat - xprev) - 0.5 * dt * (f + f_prev)
             C = jacobian_rows(D, Phi_t, dt)
-            dx = np.linalg.lstsq(A @ C, -(A @ r), rcond=None)[0]    # R10
-            g = np.linalg.norm(C.T @ r)
+            AC, Ar = A @ C, A @ r                                    # R10
+            dx = np.linalg.lstsq(AC, -Ar, rcond=None)[0]
+            g = np.linalg.norm(AC.T @ Ar)                            # R9
             first = g if first is None else first
             xhat = xhat + dx
             k += 1

@@ -74,6 +74,19 @@ def fom_params(dt, delta, mode="blockdiag", tol=None, max_iter=100, p_it=None, p
                      _prec(prec), int(gmres_restart), int(gmres_max_iter), float(gmres_rtol))
 
 
+class ModelDesc(ctypes.Structure):
+    """Mirror of ptrom_model_desc (host arrays are pointers)."""
+    _fields_ = [("n_s", _i), ("M", _i), ("M_r", _i), ("N_c", _i), ("dt", _d), ("delta", _d),
+                ("tol", _d), ("max_gn", _i), ("qr_prec", _i),
+                ("phi_s", _vp), ("x0_s", _vp), ("phi_c", _vp), ("x0_c", _vp), ("gamma_c", _vp),
+                ("A", _vp), ("off", _vp), ("idx", _vp)]
+
+
+class PtromStats(ctypes.Structure):
+    _fields_ = [("gn_iters", ctypes.c_longlong), ("steps", ctypes.c_longlong), ("noconv", _i),
+                ("max_iters", _i)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -90,6 +103,12 @@ def _load():
         "ptrom_launch_count": ([], ctypes.c_longlong),
         "ptrom_timing_enable": ([_i], _i),
         "ptrom_timing_read": ([ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i], _i),
+        "ptrom_model_create": ([ctypes.POINTER(ModelDesc), ctypes.POINTER(_vp)], _i),
+        "ptrom_free": ([_vp], None),
+        "ptrom_set_param": ([_vp, _vp, _vp, _vp, _vp], _i),
+        "ptrom_state_bytes": ([_vp], ctypes.c_size_t),
+        "ptrom_step": ([ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                        ctypes.POINTER(_vp), _i, ctypes.POINTER(PtromStats), _vp], _i),
         "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
         "fom_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                       ctypes.POINTER(FomStats), _vp], _i),
@@ -232,3 +251,65 @@ def fom_step(params, Gamma, x, f, work=None, stream=None, allow_noconv=False):
     d = st.as_dict()
     d["converged"] = True
     return d
+
+
+# ----------------------------------------------------------------- PTROM
+def _host(a, dtype):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class PtromModel:
+    """A PTROM online model on the current device (ptrom_model_create).
+
+    Arrays are host (NumPy) arrays in the layouts of include/ptrom.h:
+    phi_s (2 n_s, M), x0_s (2 n_s), phi_c (2 N_c, M), x0_c (2 N_c),
+    gamma_c (N_c), A (M_r, 2 n_s), CSR lists off (n_s+1) / idx."""
+
+    def __init__(self, phi_s, x0_s, phi_c, x0_c, gamma_c, A, off, idx, dt, delta, tol=1e-4,
+                 max_gn=100, qr_prec="fp64"):
+        import numpy as np
+        keep = [_host(phi_s, np.float64), _host(x0_s, np.float64), _host(phi_c, np.float64),
+                _host(x0_c, np.float64), _host(gamma_c, np.float64), _host(A, np.float64),
+                _host(off, np.int32), _host(idx, np.int32)]
+        ns = keep[1].size // 2
+        M = keep[0].shape[1]
+        Mr = keep[5].shape[0]
+        Nc = keep[4].size
+        d = ModelDesc(ns, M, Mr, Nc, float(dt), float(delta), float(tol), int(max_gn), _prec(qr_prec),
+                      *[ctypes.c_void_p(a.ctypes.data) for a in keep])
+        h = ctypes.c_void_p()
+        _check(lib.ptrom_model_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.n_s, self.M, self.M_r, self.N_c = ns, M, Mr, Nc
+
+    def set_param(self, x0_s=None, phi_c=None, x0_c=None, gamma_c=None):
+        import numpy as np
+        arrs = [None if a is None else _host(a, np.float64) for a in (x0_s, phi_c, x0_c, gamma_c)]
+        _check(lib.ptrom_set_param(self.handle,
+                                   *[None if a is None else ctypes.c_void_p(a.ctypes.data) for a in arrs]))
+
+    def new_state(self, device="cuda"):
+        """Zero state: xhat = 0, carried velocity computed on the first step."""
+        nbytes = lib.ptrom_state_bytes(self.handle)
+        return torch.zeros(int(nbytes), dtype=torch.uint8, device=device)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.ptrom_free(h)
+            self.handle = None
+
+
+def ptrom_step(models, states, nsteps, xhat=None, hist=None, stream=None, want_stats=True):
+    """Advance len(models) instances by nsteps in one launch.  models: list of
+    PtromModel; states: list of uint8 device tensors from new_state();
+    xhat / hist: optional lists of float64 device tensors (M) / (nsteps, M)."""
+    b = len(models)
+    arr = lambda xs: (_vp * b)(*[ctypes.c_void_p(x.data_ptr()) for x in xs])
+    mh = (_vp * b)(*[m.handle for m in models])
+    st = PtromStats()
+    _check(lib.ptrom_step(mh, b, arr(states), arr(xhat) if xhat is not None else None,
+                          arr(hist) if hist is not None else None, int(nsteps),
+                          ctypes.byref(st) if want_stats else None, _stream(stream)))
+    return {k: getattr(st, k) for k, _ in st._fields_} if want_stats else None

@@ -1,0 +1,36 @@
+"""Oracle-built PTROM models for the tests and the benchmark's CPU leg.
+
+Runs the paper's offline stages with the FP64 oracle (Stage 1 FOM snapshots,
+Stage 2 POD + ClusterPOD, Stage 3 Tier-II LSPG residual snapshots, Stage 4
+greedy sampling) and returns the arrays the library's model takes."""
+import numpy as np
+
+from oracle import fom, rom
+
+
+def build_case(x0, G, delta, dt, steps, M, n_s, M_r, criterion="bh", theta=0.5, p_c=1.0,
+               tol=1e-4, fom_mode="dense"):
+    N = G.size
+    traj, _ = fom.rollout(x0, G, delta, dt, steps, mode=fom_mode, tol=1e-12)
+    S = (traj[1:] - x0).T                                       # R1
+    Phi, sig = rom.pod(S, M)
+    cl_all, _ = rom.cluster_tables(Phi, sig, x0, G, np.arange(N), criterion=criterion,
+                                   theta=theta, p_c=p_c)
+    _, snaps = rom.lspg_tier2(cl_all, Phi, x0, delta, dt, steps, tol=tol)
+    Phi_r, _ = rom.pod(snaps, M_r)
+    sampled = rom.greedy_sample(Phi_r, n_s, N)
+    A = rom.gappy_operator(Phi_r, sampled, N)
+    cl, _ = rom.cluster_tables(Phi, sig, x0, G, sampled, criterion=criterion, theta=theta, p_c=p_c)
+    return dict(traj=traj, Phi=Phi, sig=sig, cl=cl, A=A, sampled=sampled, x0=x0, G=G,
+                delta=delta, dt=dt)
+
+
+def model_arrays(case):
+    """Arrays in the layouts of include/ptrom.h for the library's model."""
+    cl, Phi, x0 = case["cl"], case["Phi"], case["x0"]
+    Phi_t, x0_t = rom.target_rows(Phi, x0, cl.targets)
+    off = np.zeros(len(cl.lists) + 1, dtype=np.int32)
+    off[1:] = np.cumsum([len(li) for li in cl.lists])
+    idx = np.concatenate([np.asarray(li, dtype=np.int32) for li in cl.lists]) if off[-1] else np.zeros(0, np.int32)
+    return dict(phi_s=Phi_t, x0_s=x0_t, phi_c=cl.Phit, x0_c=cl.x0t, gamma_c=cl.Gt, A=case["A"],
+                off=off, idx=idx)
