@@ -288,6 +288,73 @@ int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
                double *const *xhat, double *const *hist, int nsteps,
                ptrom_stats *stats, ptrom_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * ptrom_build -- the offline training of Sec. 5.1 for one or more training
+ * parameters mu_p (circulations Gamma_p, initial states x0_p):
+ *   Stage 1  FOM snapshots x^n(mu_p) - x^0(mu_p), n = 1..steps (fom_step
+ *            with the given FOM parameters);
+ *   Stage 2  POD Phi (M modes, Sec. 3.1) of all snapshots; the quadtree of
+ *            the weighted POD space W = Phi sigma (Sec. 4.1.1) and the source
+ *            clusters of every body (Alg. 2 with Alg. 3: Barnes-Hut theta or
+ *            neighbour p_c);
+ *   Stage 3  Tier-II LSPG (Eq. GNLinearLeastSquares) over all bodies with the
+ *            clustered sources, the inexact block-diagonal Jacobian and
+ *            alpha = 1, collecting the residual at every Gauss-Newton iterate;
+ *            residual POD Phi_r (M_r modes);
+ *   Stage 4  greedy sampling of n_s bodies (Alg. 1), A = [P Phi_r]^+.
+ * The returned online model is set to the first training parameter; use
+ * ptrom_set_param_full for any other mu.
+ * All input arrays are DEVICE arrays: x0s [n_params][2n], gammas
+ * [n_params][n].  Limits of this build: n_params * steps <= 4096 snapshots,
+ * n <= 65536.  Synchronises the stream (the host runs the tree and the small
+ * dense algebra).
+ * ------------------------------------------------------------------------ */
+enum ptrom_criterion { PTROM_BARNES_HUT = 0, PTROM_NEIGHBOR = 1 };
+
+typedef struct ptrom_build_params {
+    int M, M_r, n_s;       /* POD rank, residual rank, sampled bodies        */
+    int criterion;         /* enum ptrom_criterion                           */
+    double theta, p_c;     /* Barnes-Hut opening ratio / neighbour factor    */
+    int steps;             /* training time steps per parameter              */
+    double tol;            /* Gauss-Newton tolerance (Tier II and online)    */
+    int max_gn;            /* Gauss-Newton cap (Tier II and online)          */
+    int qr_prec;           /* online least-squares precision                 */
+    ptrom_fom_params fom;  /* Stage 1 FOM (dt and delta are the model's)     */
+} ptrom_build_params;
+
+typedef struct ptrom_build_info {
+    int n_snapshots, n_res_snapshots;  /* Stage 1 / Stage 3 columns          */
+    int N_c;                           /* unique clusters of the sampled bodies */
+    int N_c_all;                       /* unique clusters over all bodies    */
+    double mean_list;                  /* mean clusters per sampled body     */
+    double mean_list_all;              /* mean clusters per body (Tier II)   */
+    double sigma_ratio;                /* sigma_M / sigma_1                   */
+    double seconds_fom, seconds_pod, seconds_tree, seconds_tier2, seconds_sample;
+} ptrom_build_info;
+
+int ptrom_build(const ptrom_build_params *p, int n, int n_params, const double *x0s,
+                const double *gammas, ptrom_model **out, ptrom_build_info *info,
+                ptrom_stream_t stream);
+
+/* Reload a built model for a new parameter from the full per-body arrays
+ * (DEVICE, [2n] and [n]): cluster circulations, POD surrogates and reference
+ * positions are recomputed from the stored memberships (Sec. 5.2), without
+ * retraining.  PTROM_EINVAL for models not made by ptrom_build. */
+int ptrom_set_param_full(ptrom_model *m, const double *x0, const double *Gamma,
+                         ptrom_stream_t stream);
+
+/* x = x^0 + Phi xhat on the listed bodies (Sec. 5.3): rows [nrows] (DEVICE
+ * int body indices), out [2 nrows] ([chi..., psi...]), xhat [M] (DEVICE).
+ * Only for models made by ptrom_build (they keep Phi and x^0). */
+int ptrom_reconstruct(const ptrom_model *m, const double *xhat, const int *rows,
+                      int nrows, double *out, ptrom_stream_t stream);
+
+/* Host copies of a built model's offline data, for inspection and tests:
+ * any pointer may be NULL.  phi [2n x M] row-major, sigma [M],
+ * sampled [n_s] (body ids in Alg. 1 order), A [M_r x 2 n_s] row-major. */
+int ptrom_model_query(const ptrom_model *m, int *n, int *M, int *M_r, int *n_s,
+                      int *N_c, double *phi, double *sigma, int *sampled, double *A);
+
 #ifdef __cplusplus
 }
 #endif

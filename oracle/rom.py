@@ -158,14 +158,17 @@ def _weighted_mean(members, Gamma, rows):
 
 
 def cluster_tables(Phi, sigma, x0, Gamma, targets, criterion="bh", theta=0.5, p_c=1.0,
-                   max_depth=40):
+                   max_depth=40, W=None):
     """Alg. 2 (WeightedMean, FindClusters/Traverse, UniqueSearch) with Alg. 3.
 
     The tree lives in the weighted POD space W = Phi sigma (Sec. 4.1.1):
-    body i is the point (W_i, W_{i+N})."""
+    body i is the point (W_i, W_{i+N}).  W may be passed in precomputed (the
+    neighbour test compares box edges that coincide in exact arithmetic, so
+    its outcome can depend on how W was rounded)."""
     N = Gamma.size
     M = Phi.shape[1]
-    W = Phi @ sigma
+    if W is None:
+        W = Phi @ sigma
     pts = np.stack([W[:N], W[N:]], axis=1)
     tree = QuadTree(pts, max_depth=max_depth)
     # WeightedMean: |Gamma|-weighted centroid of each node in W (R4)

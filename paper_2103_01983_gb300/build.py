@@ -21,6 +21,7 @@ ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+           "-Xcompiler", "-ffp-contract=off",
            "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

@@ -34,6 +34,7 @@ inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_
 // does not map and unmap memory at every synchronisation).
 int scratch_alloc(void **ptr, size_t bytes, cudaStream_t st);
 int scratch_free(void *ptr, cudaStream_t st);
+int scratch_trim();  // release the current device pool's cached blocks
 // CUDA-event timing of one launch (no-op unless ptrom_timing_enable(1)).
 int timing_begin(int kind, cudaStream_t st);
 void timing_end(int slot, cudaStream_t st);

@@ -30,32 +30,9 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "ptrom_model.h"
 
 namespace ptrom {
-
-constexpr int kPT = 512;  // threads per instance
-constexpr int kMaxM = 64, kMaxMr = 128, kMaxNs = 512, kMaxNc = 8192;
-constexpr int kTileB = 16;  // bodies per A C tile (32 dofs)
-
-struct DevModel {
-    int ns, M, Mr, Nc, Mp, Mrp;
-    double dt, delta, tol;
-    int max_gn, qr64;
-    const float *phiB;  // [2ns][Mp]
-    const float *x0B;   // [2ns]   relative to origin
-    const float *phiT;  // [2Nc][Mp]
-    const float *x0T;   // [2Nc]   relative to origin
-    const float *gT;    // [Nc]    Gamma~ / (2 pi)
-    const int *off, *idx;
-    const float *At;    // [2ns][Mrp]  (A transposed, zero padded)
-};
-
-struct InstArgs {
-    DevModel m;
-    double *state;  // [M] xhat, [2ns] carried velocity, [8] flags (as doubles)
-    double *xhat;
-    double *hist;
-};
 
 struct DevStats {
     unsigned long long gn_iters, steps;
@@ -413,14 +390,6 @@ k_ptrom(const InstArgs *__restrict__ insts, int nsteps, DevStats *stats) {
 }  // namespace ptrom
 
 // ------------------------------------------------------------------ host side
-struct ptrom_model {
-    ptrom::DevModel d;
-    int device;
-    double ox, oy;
-    std::vector<void *> bufs;
-    size_t smem;
-};
-
 using namespace ptrom;
 
 static int upload(ptrom_model *m, const void *host, size_t bytes, void **out) {
@@ -440,7 +409,7 @@ static std::vector<float> to_f32_rows(const double *a, int rows, int cols, int l
     return o;
 }
 
-static int fill_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
+int ptrom::model_fill_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
                       const double *gamma_c) {
     DevModel &d = m->d;
     if (x0_s) {
@@ -542,7 +511,7 @@ extern "C" int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **ou
         if ((st = upload(m, At.data(), At.size() * 4, &p))) return fail(st);
         d.At = (const float *)p;
     }
-    if ((st = fill_param(m, s.x0_s, s.phi_c, s.x0_c, s.gamma_c))) return fail(st);
+    if ((st = model_fill_param(m, s.x0_s, s.phi_c, s.x0_c, s.gamma_c))) return fail(st);
     *out = m;
     return PTROM_OK;
 }
@@ -556,7 +525,7 @@ extern "C" void ptrom_free(ptrom_model *m) {
 extern "C" int ptrom_set_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
                                const double *gamma_c) {
     if (!m) return set_error(PTROM_EINVAL, "ptrom_set_param: NULL model");
-    return fill_param(m, x0_s, phi_c, x0_c, gamma_c);
+    return model_fill_param(m, x0_s, phi_c, x0_c, gamma_c);
 }
 
 extern "C" size_t ptrom_state_bytes(const ptrom_model *m) {

@@ -1,0 +1,60 @@
+// Internal layout of a PTROM online model, shared by ptrom.cu (online step)
+// and ptrom_build.cu (offline training).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace ptrom {
+
+constexpr int kPT = 512;  // threads per instance
+constexpr int kMaxM = 64, kMaxMr = 128, kMaxNs = 512, kMaxNc = 8192;
+constexpr int kTileB = 16;  // bodies per A C tile (32 dofs)
+
+struct DevModel {
+    int ns, M, Mr, Nc, Mp, Mrp;
+    double dt, delta, tol;
+    int max_gn, qr64;
+    const float *phiB;  // [2ns][Mp]
+    const float *x0B;   // [2ns]   relative to origin
+    const float *phiT;  // [2Nc][Mp]
+    const float *x0T;   // [2Nc]   relative to origin
+    const float *gT;    // [Nc]    Gamma~ / (2 pi)
+    const int *off, *idx;
+    const float *At;    // [2ns][Mrp]  (A transposed, zero padded)
+};
+
+struct InstArgs {
+    DevModel m;
+    double *state;  // [M] xhat, [2ns] carried velocity, [8] flags (as doubles)
+    double *xhat;
+    double *hist;
+};
+
+}  // namespace ptrom
+
+struct ptrom_model {
+    ptrom::DevModel d;
+    int device;
+    double ox, oy;
+    std::vector<void *> bufs;
+    size_t smem;
+    // offline data, kept by models made with ptrom_build
+    bool built = false;
+    int n = 0;
+    std::vector<double> phi;      // [2n][M] row-major
+    std::vector<double> sigma;    // [M]
+    std::vector<int> sampled;     // [n_s]
+    std::vector<double> A;        // [M_r][2 n_s] row-major
+    std::vector<int> cl_off;      // [N_c + 1] cluster -> members (CSR)
+    std::vector<int> cl_mem;
+    double *phi_dev = nullptr;    // [2n][M] FP64 (reconstruction)
+    double *x0_dev = nullptr;     // [2n]
+};
+
+namespace ptrom {
+// Fill the parameter-dependent device arrays of a model from host arrays.
+int model_fill_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
+                     const double *gamma_c);
+}  // namespace ptrom

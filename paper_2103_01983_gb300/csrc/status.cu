@@ -156,4 +156,11 @@ int scratch_free(void *ptr, cudaStream_t st) {
     PTROM_CUDA(cudaFreeAsync(ptr, st));
     return PTROM_OK;
 }
+
+int scratch_trim() {
+    cudaMemPool_t pool;
+    PTROM_TRY(pool_for_current(&pool));
+    PTROM_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return PTROM_OK;
+}
 }  // namespace ptrom

@@ -87,6 +87,19 @@ class PtromStats(ctypes.Structure):
                 ("max_iters", _i)]
 
 
+class BuildParams(ctypes.Structure):
+    """Mirror of ptrom_build_params."""
+    _fields_ = [("M", _i), ("M_r", _i), ("n_s", _i), ("criterion", _i), ("theta", _d), ("p_c", _d),
+                ("steps", _i), ("tol", _d), ("max_gn", _i), ("qr_prec", _i), ("fom", FomParams)]
+
+
+class BuildInfo(ctypes.Structure):
+    """Mirror of ptrom_build_info."""
+    _fields_ = [("n_snapshots", _i), ("n_res_snapshots", _i), ("N_c", _i), ("N_c_all", _i),
+                ("mean_list", _d), ("mean_list_all", _d), ("sigma_ratio", _d), ("seconds_fom", _d),
+                ("seconds_pod", _d), ("seconds_tree", _d), ("seconds_tier2", _d), ("seconds_sample", _d)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -109,6 +122,11 @@ def _load():
         "ptrom_state_bytes": ([_vp], ctypes.c_size_t),
         "ptrom_step": ([ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                         ctypes.POINTER(_vp), _i, ctypes.POINTER(PtromStats), _vp], _i),
+        "ptrom_build": ([ctypes.POINTER(BuildParams), _i, _i, _vp, _vp, ctypes.POINTER(_vp),
+                         ctypes.POINTER(BuildInfo), _vp], _i),
+        "ptrom_set_param_full": ([_vp, _vp, _vp, _vp], _i),
+        "ptrom_reconstruct": ([_vp, _vp, _vp, _i, _vp, _vp], _i),
+        "ptrom_model_query": ([_vp] + [ctypes.POINTER(_i)] * 5 + [_vp, _vp, _vp, _vp], _i),
         "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
         "fom_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                       ctypes.POINTER(FomStats), _vp], _i),
@@ -289,6 +307,40 @@ class PtromModel:
         _check(lib.ptrom_set_param(self.handle,
                                    *[None if a is None else ctypes.c_void_p(a.ctypes.data) for a in arrs]))
 
+    @classmethod
+    def _wrap(cls, handle):
+        obj = cls.__new__(cls)
+        obj.handle = handle
+        vals = [_i() for _ in range(5)]
+        _check(lib.ptrom_model_query(handle, *[ctypes.byref(v) for v in vals], None, None, None, None))
+        obj.n, obj.M, obj.M_r, obj.n_s, obj.N_c = [v.value for v in vals]
+        return obj
+
+    def query(self):
+        """Offline data of a built model: phi (2n, M), sigma (M), sampled (n_s), A (M_r, 2 n_s)."""
+        import numpy as np
+        phi = np.empty((2 * self.n, self.M))
+        sig = np.empty(self.M)
+        smp = np.empty(self.n_s, dtype=np.int32)
+        A = np.empty((self.M_r, 2 * self.n_s))
+        _check(lib.ptrom_model_query(self.handle, None, None, None, None, None,
+                                     ctypes.c_void_p(phi.ctypes.data), ctypes.c_void_p(sig.ctypes.data),
+                                     ctypes.c_void_p(smp.ctypes.data), ctypes.c_void_p(A.ctypes.data)))
+        return {"phi": phi, "sigma": sig, "sampled": smp, "A": A}
+
+    def set_param_full(self, x0, Gamma, stream=None):
+        """Reload the clusters for a new parameter (device x0 [2n], Gamma [n])."""
+        _check(lib.ptrom_set_param_full(self.handle, _ptr(x0), _ptr(Gamma), _stream(stream)))
+
+    def reconstruct(self, xhat, rows=None, stream=None):
+        """x = x^0 + Phi xhat on the listed bodies (default all) -> [chi..., psi...]."""
+        if rows is None:
+            rows = torch.arange(self.n, dtype=torch.int32, device=xhat.device)
+        out = torch.empty(2 * rows.numel(), dtype=torch.float64, device=xhat.device)
+        _check(lib.ptrom_reconstruct(self.handle, _ptr(xhat), ctypes.c_void_p(rows.data_ptr()), rows.numel(),
+                                     _ptr(out), _stream(stream)))
+        return out
+
     def new_state(self, device="cuda"):
         """Zero state: xhat = 0, carried velocity computed on the first step."""
         nbytes = lib.ptrom_state_bytes(self.handle)
@@ -313,3 +365,22 @@ def ptrom_step(models, states, nsteps, xhat=None, hist=None, stream=None, want_s
                           arr(hist) if hist is not None else None, int(nsteps),
                           ctypes.byref(st) if want_stats else None, _stream(stream)))
     return {k: getattr(st, k) for k, _ in st._fields_} if want_stats else None
+
+
+CRITERIA = {"bh": 0, "barnes_hut": 0, "nb": 1, "neighbor": 1}
+
+
+def ptrom_build(x0s, gammas, M, M_r, n_s, steps, fom, criterion="bh", theta=0.5, p_c=1.0, tol=1e-4,
+                max_gn=100, qr_prec="fp64", stream=None):
+    """Offline training (Stages 1-4) from device tensors x0s [P, 2n], gammas [P, n].
+    Returns (PtromModel, info dict)."""
+    x0s = x0s.contiguous()
+    gammas = gammas.contiguous()
+    P, n = gammas.shape
+    bp = BuildParams(int(M), int(M_r), int(n_s), CRITERIA[criterion], float(theta), float(p_c), int(steps),
+                     float(tol), int(max_gn), _prec(qr_prec), fom)
+    h = ctypes.c_void_p()
+    info = BuildInfo()
+    _check(lib.ptrom_build(ctypes.byref(bp), int(n), int(P), _ptr(x0s), _ptr(gammas), ctypes.byref(h),
+                           ctypes.byref(info), _stream(stream)))
+    return PtromModel._wrap(h), {k: getattr(info, k) for k, _ in info._fields_}
