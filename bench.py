@@ -13,6 +13,11 @@ region starts; the 129 MB L2 is flushed (256 MB memset) before every timed
 step.  With --impl reference the FP64 CPU oracle is timed instead on the host
 cores (a bounded sample of the same workload).
 
+The JSON line also carries the PTROM-vs-GPU-FOM step speed-up on the same
+workload ("ptrom"): a model trained by ptrom_build (untimed) is stepped
+online for one instance and for a batch of one instance per SM, with its QoI
+errors against the GPU FOM.
+
 Multi-GPU: every rank runs an independent replica (the FOM step of one
 instance does not shard on this hardware); value = all ranks' pairs / the
 slowest rank's time (weak scaling).
@@ -292,12 +297,105 @@ def run_ours(args):
         "step_stats": {k: v / args.steps for k, v in agg.items()},
         "kernels": kernels,
     }
+    if rank == 0 and not args.no_ptrom:
+        line["ptrom"] = ptrom_leg(ptrom, dev, ms_all / args.steps)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return line if rank == 0 else None
+
+
+def _hamiltonian_gpu(x, G, n):
+    """H = 1/(4 pi) sum_j sum_{i != j} Gamma_i Gamma_j log |x_i - x_j| (Sec. 6.1), on the GPU."""
+    import torch
+    chi, psi = x[:n], x[n:]
+    H = torch.zeros((), dtype=torch.float64, device=x.device)
+    for a in range(0, n, 4096):
+        dx = chi[a:a + 4096, None] - chi[None, :]
+        dy = psi[a:a + 4096, None] - psi[None, :]
+        r2 = dx * dx + dy * dy
+        r2[r2 == 0] = 1.0                      # log 1 = 0 removes i == j
+        H = H + (G[a:a + 4096, None] * G[None, :] * 0.5 * torch.log(r2)).sum()
+    return float(H) / (4.0 * 3.141592653589793)
+
+
+def ptrom_leg(ptrom, dev, fom_ms_per_step, steps=200):
+    """PTROM-vs-GPU-FOM step speed-up on the benchmarked workload.
+
+    Offline (untimed): ptrom_build trains reproductively on `steps` FOM steps
+    (POD rank 20, residual rank 40, 40 sampled bodies, Barnes-Hut theta 0.5).
+    Online (timed): `steps` PTROM steps in one launch for one instance, and
+    for a batch of 152 instances (one per SM).  QoI errors (MAE_D, AE_H of
+    Sec. 6.1) against the GPU FOM at every 50th step."""
+    import numpy as np
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    n, delta, dt = WORKLOAD["n_bodies"], WORKLOAD["delta"], WORKLOAD["dt"]
+    x0, G = W.two_cluster(n, seed=0)
+    x0d = torch.tensor(x0, device=dev)
+    Gd = torch.tensor(G, device=dev)
+    fp = ptrom.fom_params(dt, delta, "jfnk", tol=WORKLOAD["newton_tol"], prec="fp32c")
+    out = {"workload": f"two-cluster N={n}, reproductive, {steps} steps, k=20, n_s=40, M_r=40, "
+                       "Barnes-Hut theta=0.5", "variants": {}}
+    # FOM reference states
+    x = x0d.clone()
+    f = ptrom.bs_velocity(x, Gd, delta)
+    work = ptrom.fom_workspace(fp, n, dev)
+    ref = {}
+    for k in range(1, steps + 1):
+        ptrom.fom_step(fp, Gd, x, f, work=work)
+        if k % 50 == 0:
+            ref[k] = x.clone()
+    H_ref = {k: _hamiltonian_gpu(v, Gd, n) for k, v in ref.items()}
+    l = float(np.hypot(x0[n - 1] - x0[0], x0[2 * n - 1] - x0[n]))
+    for qr in ("fp64", "fp32c"):
+        t0 = time.perf_counter()
+        model, info = ptrom.ptrom_build(x0d[None], Gd[None], 20, 40, 40, steps, fp, criterion="bh", theta=0.5,
+                                        tol=1e-4, qr_prec=qr)
+        build_s = time.perf_counter() - t0
+        M = model.M
+        st = model.new_state(dev)
+        hist = torch.zeros(steps, M, dtype=torch.float64, device=dev)
+        ptrom.ptrom_step([model], [model.new_state(dev)], 5)   # warm-up launch
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ptrom.ptrom_step([model], [st], steps, hist=[hist], want_stats=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        us_step = 1e3 * e0.elapsed_time(e1) / steps
+        stats = ptrom.ptrom_step([model], [model.new_state(dev)], steps)
+        # batched: one instance per SM in one launch
+        B = torch.cuda.get_device_properties(dev).multi_processor_count
+        sts = [model.new_state(dev) for _ in range(B)]
+        ptrom.ptrom_step([model] * B, sts, 5)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        ptrom.ptrom_step([model] * B, sts, steps, want_stats=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        batch_ms = e0.elapsed_time(e1)
+        mae, aeh = [], []
+        for k, xr in ref.items():
+            xp = model.reconstruct(hist[k - 1])
+            d = torch.sqrt((xp[:n] - xr[:n]) ** 2 + (xp[n:] - xr[n:]) ** 2)
+            mae.append(float(d.sum()) / (l * n))
+            aeh.append(abs(_hamiltonian_gpu(xp, Gd, n) - H_ref[k]) / abs(H_ref[k]))
+        out["variants"][f"qr_{qr}"] = {
+            "build_s": build_s, "N_c": info["N_c"], "mean_clusters_per_sampled_body": info["mean_list"],
+            "ptrom_us_per_step": us_step, "fom_ms_per_step": fom_ms_per_step,
+            "speedup_vs_gpu_fom_step": fom_ms_per_step * 1e3 / us_step,
+            "gn_iters_per_step": stats["gn_iters"] / max(stats["steps"], 1), "noconv_steps": stats["noconv"],
+            "batched_instances": B, "batched_solves_per_s": B * steps / (batch_ms * 1e-3),
+            "batched_speedup_vs_gpu_fom_step": B * steps / (batch_ms * 1e-3) * fom_ms_per_step * 1e-3,
+            "qoi_vs_gpu_fom": {"mae_d_max": max(mae), "ae_h_max": max(aeh), "steps_checked": sorted(ref)},
+        }
+        del model
+    return out
 
 
 def _traffic(kind, n):
@@ -382,6 +480,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ptrom", action="store_true", help="skip the PTROM speed-up leg")
     ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")

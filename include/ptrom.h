@@ -291,8 +291,8 @@ int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
 /* ------------------------------------------------------------------------
  * ptrom_build -- the offline training of Sec. 5.1 for one or more training
  * parameters mu_p (circulations Gamma_p, initial states x0_p):
- *   Stage 1  FOM snapshots x^n(mu_p) - x^0(mu_p), n = 1..steps (fom_step
- *            with the given FOM parameters);
+ *   Stage 1  FOM snapshots: the states x^n(mu_p), n = 1..steps (fom_step
+ *            with the given FOM parameters), as Sec. 3.1 defines them;
  *   Stage 2  POD Phi (M modes, Sec. 3.1) of all snapshots; the quadtree of
  *            the weighted POD space W = Phi sigma (Sec. 4.1.1) and the source
  *            clusters of every body (Alg. 2 with Alg. 3: Barnes-Hut theta or

@@ -23,8 +23,12 @@ Pieces, in the paper's order and notation:
                            bodies).
 
 Readings where the paper is silent or garbled (each used by the CUDA path too):
-  R1 snapshots are offsets x^n - x^0(mu), so x = x^0 + Phi xhat can reproduce
-     them (the approximation is x^0 + Phi xhat).
+  R1 snapshots are the states themselves, S = [x^1 .. x^Nt] (Sec. 3.1 as
+     printed), not offsets from x^0: the leading POD mode is then close to the
+     mean configuration, so the weighted POD space W = Phi sigma is close to
+     the bodies' positions and its quadtree groups physically neighbouring
+     bodies.  (With offsets W holds only displacement patterns and the
+     clustering loses most of its accuracy.)
   R2 singular-vector sign: each column's largest-magnitude entry is positive.
   R3 tree: square root cell (bounding box padded to its longest side), midpoint
      split into four, leaf = one body, depth cap 40 (then a leaf may hold more).

@@ -4,8 +4,8 @@
 // GPU: FOM training runs (fom_step), the FP64 snapshot Gram matrix and basis
 // products, and Tier-II LSPG over all bodies (cluster gather, warp-per-body
 // pair sums with the residual, normal equations of the Gauss-Newton least
-// squares).  Host C++: the symmetric eigen-solver of the Gram matrix (cyclic
-// Jacobi), the quadtree over the weighted POD space with WeightedMean,
+// squares).  Host C++: the symmetric eigen-solver of the Gram matrix
+// (tridiagonal + QL, symeig.h), the quadtree over the weighted POD space with WeightedMean,
 // FindClusters/checkPrune and UniqueSearch (Alg. 2/3), the greedy sampling
 // (Alg. 1) and the gappy pseudo-inverse; their sizes are O(N) or tiny.
 #include <math.h>
@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "ptrom_model.h"
+#include "symeig.h"
 
 namespace ptrom {
 namespace {
@@ -181,9 +182,9 @@ __global__ void k_combine(int nd, int K, int M, const double *__restrict__ S, co
     }
 }
 
-// x - x0 as one snapshot column
-__global__ void k_diff(int nd, const double *x, const double *x0, double *out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) out[i] = x[i] - x0[i];
+// one snapshot column: the state x^n itself (Sec. 3.1)
+__global__ void k_snapshot(int nd, const double *x, double *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) out[i] = x[i];
 }
 
 struct T2 {
@@ -532,7 +533,7 @@ int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vec
     for (int a = 0; a < K; ++a)
         for (int b = 0; b < a; ++b) Gh[(size_t)a * K + b] = Gh[(size_t)b * K + a];
     std::vector<double> w, V;
-    jacobi_eig(K, Gh, w, V);
+    if (!symeig(K, Gh, w, V)) jacobi_eig(K, Gh, w, V);  // Jacobi as the slow, always-convergent fallback
     if (clamp) {
         int r = 0;
         while (r < M && w[r] > 1e-24 * w[0]) ++r;
@@ -678,7 +679,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
         for (int s = 0; s < p->steps; ++s) {
             const int stt = fom_step(&p->fom, n, G, x, f, work, wbytes, nullptr, stream);
             if (stt != PTROM_OK && stt != PTROM_ENOCONV) return stt;
-            k_diff<<<(nd + 255) / 256, 256, 0, st>>>(nd, x, x0, S + (size_t)(q * p->steps + s) * nd);
+            k_snapshot<<<(nd + 255) / 256, 256, 0, st>>>(nd, x, S + (size_t)(q * p->steps + s) * nd);
             count_launch();
         }
     }

@@ -12,7 +12,7 @@ def build_case(x0, G, delta, dt, steps, M, n_s, M_r, criterion="bh", theta=0.5, 
                tol=1e-4, fom_mode="dense"):
     N = G.size
     traj, _ = fom.rollout(x0, G, delta, dt, steps, mode=fom_mode, tol=1e-12)
-    S = (traj[1:] - x0).T                                       # R1
+    S = traj[1:].T                                              # R1: the states x^1..x^Nt
     Phi, sig = rom.pod(S, M)
     cl_all, _ = rom.cluster_tables(Phi, sig, x0, G, np.arange(N), criterion=criterion,
                                    theta=theta, p_c=p_c)

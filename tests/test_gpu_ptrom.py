@@ -142,12 +142,11 @@ def test_exactness_without_clustering(P):
     """Basis spans the trajectory, every body sampled, no clustering: the GPU
     PTROM reproduces the FOM (to FP32 pair-sum accuracy)."""
     from oracle import fom
-    n, steps, dt, delta = 40, 10, 0.01, 0.05
+    n, steps, dt, delta = 20, 50, 0.01, 0.05
     x0, G = W.disk(n, seed=7)
     traj, _ = fom.rollout(x0, G, delta, dt, steps, mode="dense", tol=1e-14)
-    S = (traj[1:] - x0).T
-    sv = np.linalg.svd(S, compute_uv=False)
-    M = int(np.sum(sv > 1e-7 * sv[0]))
+    S = traj[1:].T
+    M = 2 * n                                   # the basis spans the state space
     Phi, sig = rom.pod(S, M)
     cl, _ = rom.cluster_tables(Phi, sig, x0, G, np.arange(n), criterion="bh", theta=0.0)
     _, snaps = rom.lspg_tier2(cl, Phi, x0, delta, dt, steps, tol=1e-10)

@@ -51,8 +51,7 @@ def test_quadtree_structure():
 def _setup(n=120, M=4, seed=3):
     x0, G = W.disk(n, seed=seed)
     traj, _ = fom.rollout(x0, G, 0.05, 0.01, 12, mode="dense", tol=1e-13)
-    S = (traj[1:] - x0).T
-    Phi, sig = rom.pod(S, M)
+    Phi, sig = rom.pod(traj[1:].T, M)
     return x0, G, Phi, sig
 
 
@@ -134,14 +133,14 @@ def test_greedy_sampling_small_case():
 
 
 def test_ptrom_reproduces_fom_when_basis_spans_trajectory():
-    """M = rank of the snapshot offsets, every body sampled, no clustering:
-    the PTROM trajectory is the FOM trajectory (Gauss-Newton tolerance)."""
-    n, steps, dt, delta = 40, 10, 0.01, 0.05
+    """A basis spanning the state space (as many independent snapshots as
+    dofs), every body sampled, no clustering: the PTROM trajectory is the FOM
+    trajectory (Gauss-Newton tolerance)."""
+    n, steps, dt, delta = 20, 50, 0.01, 0.05
     x0, G = W.disk(n, seed=7)
     traj, _ = fom.rollout(x0, G, delta, dt, steps, mode="dense", tol=1e-14)
-    S = (traj[1:] - x0).T
-    sv = np.linalg.svd(S, compute_uv=False)
-    M = int(np.sum(sv > 1e-12 * sv[0]))       # numerical rank (<= steps)
+    S = traj[1:].T
+    M = 2 * n                                 # all left singular vectors: Phi spans R^(2n)
     Phi, sig = rom.pod(S, M)
     cl, _ = rom.cluster_tables(Phi, sig, x0, G, np.arange(n), criterion="bh", theta=0.0)
     red2, snaps = rom.lspg_tier2(cl, Phi, x0, delta, dt, steps, tol=1e-12)
