@@ -148,6 +148,18 @@ int bs_vjp(int n, const double *x, const double *Gamma, double delta,
            const double *w, double *gx_out, double *gGamma_out, int prec,
            ptrom_stream_t stream);
 
+/*
+ * bs_jphi -- the kernel Jacobian applied to every column of a basis,
+ *     out = (d f / d x) Phi,   (J Phi)_i = sum_{j != i} gamma_j A(x_i - x_j) (Phi_i - Phi_j),
+ * the J Phi of the LSPG Gauss-Newton least squares (Sec. 3.2, Eq.
+ * GNLinearLeastSquares) with the exact kernel Jacobian.
+ *   phi, out  [2n x M], column-major (column m is a state-layout vector at
+ *             phi + m*2n).  x [2n], Gamma [n].
+ * Errors: n < 2, M < 1, delta < 0, NULL arrays, bad prec -> PTROM_EINVAL.
+ */
+int bs_jphi(int n, const double *x, const double *Gamma, double delta,
+            const double *phi, int M, double *out, int prec, ptrom_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Full-order model (FOM): one implicit trapezoid step (Sec. 2, Eq. linKstep
  * with k=1, alpha0=1, alpha1=-1, beta0=beta1=1/2):

@@ -15,5 +15,8 @@ int jvp(int n, const double *x, const double *G, double delta, const double *v, 
 int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
         double *gG, int prec, cudaStream_t st, int split, void *scratch = nullptr);
 size_t pack_scratch_bytes(int ns);
+// J Phi (jphi.cu); split = source split over gridDim.z (0 = automatic).
+int jphi(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out, int prec,
+         cudaStream_t st, int split);
 
 }  // namespace ptrom

@@ -113,6 +113,7 @@ def _load():
         "bs_velocity_noalloc": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_jvp": ([_i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_vjp": ([_i, _vp, _vp, _d, _vp, _vp, _vp, _i, _vp], _i),
+        "bs_jphi": ([_i, _vp, _vp, _d, _vp, _i, _vp, _i, _vp], _i),
         "ptrom_launch_count": ([], ctypes.c_longlong),
         "ptrom_timing_enable": ([_i], _i),
         "ptrom_timing_read": ([ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i], _i),
@@ -234,6 +235,18 @@ def bs_jvp(x, Gamma, delta, v, out=None, prec="fp32c", stream=None):
     _check(lib.bs_jvp(n, _ptr(x), _ptr(Gamma), float(delta), _ptr(v), _ptr(out), _prec(prec),
                       _stream(stream)))
     return out
+
+
+def bs_jphi(x, Gamma, delta, phi, prec="fp32c", stream=None):
+    """(d f / d x) Phi for phi of shape (2n, M); returns (2n, M).  The library
+    takes column-major storage, i.e. a contiguous (M, 2n) buffer."""
+    n = Gamma.numel()
+    M = phi.shape[1]
+    cols = phi.t().contiguous()
+    out = torch.empty_like(cols)
+    _check(lib.bs_jphi(n, _ptr(x), _ptr(Gamma), float(delta), _ptr(cols), M, _ptr(out), _prec(prec),
+                       _stream(stream)))
+    return out.t()
 
 
 def bs_vjp(x, Gamma, delta, w, want_x=True, want_gamma=True, prec="fp32c", stream=None):

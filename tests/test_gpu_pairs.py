@@ -160,3 +160,30 @@ def test_full_size_sampled_rows(P, n):
     gxo, gGo = direct.vjp(x, G, delta, w, rows=rows)
     assert _rel(gx.cpu().numpy()[idx], gxo) <= 1e-5
     assert _rel(gG.cpu().numpy()[rows], gGo) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+@pytest.mark.parametrize("n,M,delta", [(1000, 20, 0.05), (777, 7, 0.0), (2050, 33, 0.02)])
+def test_jphi(P, prec, n, M, delta):
+    if delta == 0.0:
+        x, G = _jittered_grid(n, seed=60)
+    else:
+        x, G = W.two_cluster(n + (n % 2), seed=61)
+    phi = W.random_vectors(x.size, M, seed=62).T          # (2n, M)
+    ref = direct.jphi(x, G, delta, phi)
+    out = P.bs_jphi(_dev(x), _dev(G), delta, _dev(phi), prec=prec).cpu().numpy()
+    assert _rel(out, ref) <= TOL[prec]
+    # every column equals the J v product of that column
+    jv = P.bs_jvp(_dev(x), _dev(G), delta, _dev(phi[:, 3]), prec=prec).cpu().numpy()
+    assert _rel(out[:, 3], jv) <= 2 * TOL[prec]
+
+
+def test_jphi_full_size_sampled_rows(P):
+    n, M = 16384, 20
+    x, G = W.two_cluster(n, seed=0)
+    phi = W.random_vectors(2 * n, M, seed=63).T
+    out = P.bs_jphi(_dev(x), _dev(G), 0.02, _dev(phi)).cpu().numpy()
+    rows = np.random.default_rng(64).choice(n, 128, replace=False)
+    idx = np.r_[rows, n + rows]
+    ref = np.stack([direct.jvp(x, G, 0.02, phi[:, m], rows=rows) for m in range(M)], axis=1)
+    assert _rel(out[idx], ref) <= 1e-5
