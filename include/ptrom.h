@@ -224,6 +224,24 @@ int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x,
              double *f, void *work, size_t work_bytes, ptrom_fom_stats *stats,
              ptrom_stream_t stream);
 
+/*
+ * fom_adjoint_step -- reverse-mode derivative of one fom_step (implicit
+ * function theorem on the trapezoid residual r(x^n, x^{n-1}, Gamma) = 0 of
+ * Eq. linKstep).  Given lambda = dL/dx^n:
+ *     mu            = (I - dt/2 J(x^n))^{-T} lambda   (GMRES on the J^T w kernel,
+ *                      right-preconditioned by the transposed self blocks)
+ *     lambda  <-      mu + dt/2 J(x^{n-1})^T mu       (= dL/dx^{n-1})
+ *     gGamma  +=      dt/2 (F(x^n) + F(x^{n-1}))^T mu,  F = d f / d Gamma.
+ * x_n, x_prev [2n]: the step's end and start states (as fom_step produced
+ * them); lambda [2n] in/out; gGamma [n] accumulated.  p's gmres_* fields and
+ * prec are used (jac_mode is ignored).  work: fom_adjoint_workspace_bytes.
+ */
+size_t fom_adjoint_workspace_bytes(const ptrom_fom_params *p, int n);
+int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *Gamma,
+                     const double *x_n, const double *x_prev, double *lambda,
+                     double *gGamma, void *work, size_t work_bytes,
+                     ptrom_fom_stats *stats, ptrom_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Projection-tree ROM (PTROM): online Gauss-Newton (Alg. 4) over the hyper-
  * reduced pairwise interaction (Alg. 5), at the sampled bodies against the

@@ -99,3 +99,22 @@ def rollout(x0, Gamma, delta, dt, steps, mode="dense", tol=1e-12, **kw):
         traj.append(x.copy())
         iters.append(k)
     return np.array(traj), np.array(iters)
+
+
+def adjoint_rollout(x0, Gamma, delta, dt, steps, lam_T, tol=1e-13):
+    """Gradient of L = lam_T . x^steps with respect to x^0 and Gamma by the
+    adjoint of each trapezoid step (implicit function theorem on Eq.
+    linKstep), with dense Jacobians:
+        mu = (I - dt/2 J(x^n))^{-T} lam,  lam <- mu + dt/2 J(x^{n-1})^T mu,
+        gGamma += dt/2 (F(x^n) + F(x^{n-1}))^T mu,  F = d f / d Gamma."""
+    traj, _ = rollout(x0, Gamma, delta, dt, steps, mode="dense", tol=tol)
+    n2 = traj.shape[1]
+    h = 0.5 * dt
+    lam = np.array(lam_T, dtype=np.float64)
+    gG = np.zeros(len(Gamma))
+    for k in range(steps, 0, -1):
+        xn, xp = traj[k], traj[k - 1]
+        mu = np.linalg.solve((np.eye(n2) - h * kernel.jacobian(xn, Gamma, delta)).T, lam)
+        gG += h * (kernel.dfdGamma(xn, Gamma, delta).T @ mu + kernel.dfdGamma(xp, Gamma, delta).T @ mu)
+        lam = mu + h * kernel.jacobian(xp, Gamma, delta).T @ mu
+    return lam, gG, traj

@@ -163,12 +163,14 @@ __global__ void k_combine(int n2, int K, const double *V, const double *y, doubl
     }
 }
 
-// Block-diagonal solve: z_i = scale * (I - hdt D_i)^{-1} v_i, added to zacc
-// when accumulate is set.  D = [D00 | D01 | D10], D11 = -D00.
+// Block-diagonal solve: z_i = scale * (I - hdt D_i)^{-1} v_i (transposed
+// blocks when transpose is set), added to z when accumulate is set.
+// D = [D00 | D01 | D10], D11 = -D00.
 __global__ void k_blockdiag(int n, const double *D, const double *v, double hdt, double scale,
-                            double *z, int accumulate) {
+                            double *z, int accumulate, int transpose) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double d00 = D[i], d01 = D[n + i], d10 = D[2 * n + i], d11 = -d00;
+        const double d00 = D[i], d11 = -d00;
+        const double d01 = transpose ? D[2 * n + i] : D[n + i], d10 = transpose ? D[n + i] : D[2 * n + i];
         const double m00 = 1.0 - hdt * d00, m01 = -hdt * d01, m10 = -hdt * d10, m11 = 1.0 - hdt * d11;
         const double det = m00 * m11 - m01 * m10;
         const double r0 = v[i], r1 = v[n + i];
@@ -393,6 +395,7 @@ static int validate(const ptrom_fom_params *p, int n) {
 
 // ---------------------------------------------------------------- solvers
 struct Ctx {
+    int transpose = 0;  // GMRES on (I - hdt J)^T (adjoint solves) instead of (I - hdt J)
     const ptrom_fom_params *p;
     int n, n2;
     const double *G;
@@ -414,7 +417,11 @@ static int fetch(const Ctx &c, const double *dev, double *host, int count) {
 
 // A y = (I - hdt J) y through the all-pairs J v kernel.
 static int apply_jvp(Ctx &c, const double *v, double *out) {
-    PTROM_TRY(jvp(c.n, c.xi, c.G, c.p->delta, v, out, c.p->prec, c.st, 0, c.W.pack));
+    if (c.transpose) {
+        PTROM_TRY(vjp(c.n, c.xi, c.G, c.p->delta, v, out, nullptr, c.p->prec, c.st, 0, c.W.pack));
+    } else {
+        PTROM_TRY(jvp(c.n, c.xi, c.G, c.p->delta, v, out, c.p->prec, c.st, 0, c.W.pack));
+    }
     if (c.stats) c.stats->jvp_evals++;
     return PTROM_OK;
 }
@@ -445,7 +452,7 @@ static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d) {
         bool done = false;
         for (int j = 0; j < m; ++j) {
             double *vj = W.V + (size_t)j * n2;
-            k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, vj, c.hdt, 1.0, W.z, 0);
+            k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, vj, c.hdt, 1.0, W.z, 0, c.transpose);
             count_launch();
             PTROM_TRY(apply_jvp(c, W.z, W.jz));
             k_lin_op<<<c.grid, 256, 0, c.st>>>(n2, W.z, W.jz, c.hdt, W.w);
@@ -501,7 +508,7 @@ static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d) {
         PTROM_CUDA(cudaMemcpyAsync(W.ydev, y.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c.st));
         k_combine<<<c.grid, 256, 0, c.st>>>(n2, K, W.V, W.ydev, W.w);
         count_launch();
-        k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, W.w, c.hdt, 1.0, d, 1);
+        k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, W.w, c.hdt, 1.0, d, 1, c.transpose);
         count_launch();
         PTROM_CUDA(cudaGetLastError());
         if (done) break;
@@ -612,7 +619,7 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
         }
         c.stats->newton_iters++;
         if (p->jac_mode == PTROM_JAC_BLOCKDIAG) {
-            k_blockdiag<<<c.grid, 256, 0, c.st>>>(n, W.D, W.r, c.hdt, -1.0, x, 1);
+            k_blockdiag<<<c.grid, 256, 0, c.st>>>(n, W.D, W.r, c.hdt, -1.0, x, 1, 0);
             count_launch();
         } else if (p->jac_mode == PTROM_JAC_JFNK) {
             PTROM_TRY(gmres(c, W.r, -1.0, W.d));
@@ -628,5 +635,82 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
         PTROM_CUDA(cudaGetLastError());
         have_jac = true;
     }
+    return PTROM_OK;
+}
+
+
+namespace ptrom {
+// ---------------------------------------------------------------- adjoint step
+// Reverse-mode derivative of one trapezoid step (implicit function theorem on
+// r(x^n, x^{n-1}, Gamma) = 0):
+//   mu          = (I - dt/2 J(x^n))^{-T} lambda          (GMRES on J^T w)
+//   lambda_prev = mu + dt/2 J(x^{n-1})^T mu
+//   gGamma     += dt/2 (F(x^n) + F(x^{n-1}))^T mu,   F = d f / d Gamma.
+__global__ void k_add(int n, const double *a, double *y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] += a[i];
+}
+__global__ void k_axpby(int n, double a, const double *x, double b, const double *y, double *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a * x[i] + b * y[i];
+}
+
+}  // namespace ptrom
+
+extern "C" size_t fom_adjoint_workspace_bytes(const ptrom_fom_params *p, int n) {
+    if (!p) return 0;
+    ptrom_fom_params q = *p;
+    q.jac_mode = PTROM_JAC_JFNK;
+    if (validate(&q, n) != PTROM_OK) return 0;
+    return layout(&q, n, nullptr).bytes + ((size_t)n * 8 + 255) / 256 * 256;
+}
+
+extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *Gamma, const double *x_n,
+                                const double *x_prev, double *lambda, double *gGamma, void *work,
+                                size_t work_bytes, ptrom_fom_stats *stats, ptrom_stream_t stream) {
+    using namespace ptrom;
+    if (!p) return set_error(PTROM_EINVAL, "fom_adjoint_step: NULL params");
+    ptrom_fom_params q = *p;
+    q.jac_mode = PTROM_JAC_JFNK;
+    PTROM_TRY(validate(&q, n));
+    if (!Gamma || !x_n || !x_prev || !lambda || !gGamma || !work)
+        return set_error(PTROM_EINVAL, "fom_adjoint_step: NULL pointer");
+    if (((uintptr_t)work) & 255) return set_error(PTROM_EINVAL, "fom_adjoint_step: work must be 256-byte aligned");
+    Ctx c{};
+    c.transpose = 1;
+    c.p = &q;
+    c.n = n;
+    c.n2 = 2 * n;
+    c.G = Gamma;
+    c.xi = x_n;
+    c.hdt = 0.5 * q.dt;
+    c.st = (cudaStream_t)stream;
+    c.W = layout(&q, n, (char *)work);
+    const size_t need = c.W.bytes + ((size_t)n * 8 + 255) / 256 * 256;
+    if (work_bytes < need)
+        return set_error(PTROM_EINVAL, "fom_adjoint_step: work has %zu bytes, needs %zu", work_bytes, need);
+    double *gtmp = (double *)((char *)work + c.W.bytes);
+    c.grid = (c.n2 + 255) / 256;
+    if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
+    c.rgrid = red_grid(c.n2);
+    ptrom_fom_stats local{};
+    c.stats = stats ? stats : &local;
+    memset(c.stats, 0, sizeof(*c.stats));
+    Work &W = c.W;
+    PTROM_CUDA(cudaMemsetAsync(W.counter, 0, 64, c.st));
+    // self blocks at x^n for the (transposed) preconditioner
+    PTROM_TRY(velocity(n, x_n, n, x_n, Gamma, q.delta, W.fxi, W.D, q.prec, c.st, 0, W.pack));
+    c.stats->velocity_evals++;
+    // mu = (I - h J_n)^{-T} lambda
+    PTROM_TRY(gmres(c, lambda, 1.0, W.d));
+    // gGamma += h F_n^T mu
+    PTROM_TRY(vjp(n, x_n, Gamma, q.delta, W.d, nullptr, gtmp, q.prec, c.st, 0, W.pack));
+    k_axpy<<<c.grid, 256, 0, c.st>>>(n, c.hdt, gtmp, gGamma);
+    count_launch();
+    // lambda_prev = mu + h J_{n-1}^T mu ;  gGamma += h F_{n-1}^T mu
+    PTROM_TRY(vjp(n, x_prev, Gamma, q.delta, W.d, W.jz, gtmp, q.prec, c.st, 0, W.pack));
+    c.stats->jvp_evals += 2;
+    k_axpby<<<c.grid, 256, 0, c.st>>>(c.n2, 1.0, W.d, c.hdt, W.jz, lambda);
+    k_axpy<<<c.grid, 256, 0, c.st>>>(n, c.hdt, gtmp, gGamma);
+    count_launch(2);
+    PTROM_CUDA(cudaGetLastError());
     return PTROM_OK;
 }

@@ -128,6 +128,9 @@ def _load():
         "ptrom_set_param_full": ([_vp, _vp, _vp, _vp], _i),
         "ptrom_reconstruct": ([_vp, _vp, _vp, _i, _vp, _vp], _i),
         "ptrom_model_query": ([_vp] + [ctypes.POINTER(_i)] * 5 + [_vp, _vp, _vp, _vp], _i),
+        "fom_adjoint_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
+        "fom_adjoint_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                              ctypes.POINTER(FomStats), _vp], _i),
         "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
         "fom_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                       ctypes.POINTER(FomStats), _vp], _i),
@@ -397,3 +400,22 @@ def ptrom_build(x0s, gammas, M, M_r, n_s, steps, fom, criterion="bh", theta=0.5,
     _check(lib.ptrom_build(ctypes.byref(bp), int(n), int(P), _ptr(x0s), _ptr(gammas), ctypes.byref(h),
                            ctypes.byref(info), _stream(stream)))
     return PtromModel._wrap(h), {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def fom_adjoint_workspace(params, n, device="cuda"):
+    nbytes = lib.fom_adjoint_workspace_bytes(ctypes.byref(params), int(n))
+    if nbytes == 0:
+        raise PtromError(EINVAL, last_error())
+    return torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+
+
+def fom_adjoint_step(params, Gamma, x_n, x_prev, lam, gGamma, work=None, stream=None):
+    """lam (dL/dx^n -> dL/dx^{n-1}) and gGamma (+= dL/dGamma share) in place."""
+    n = Gamma.numel()
+    if work is None:
+        work = fom_adjoint_workspace(params, n, x_n.device)
+    st = FomStats()
+    _check(lib.fom_adjoint_step(ctypes.byref(params), n, _ptr(Gamma), _ptr(x_n), _ptr(x_prev), _ptr(lam),
+                                _ptr(gGamma), ctypes.c_void_p(work.data_ptr()), work.numel(), ctypes.byref(st),
+                                _stream(stream)))
+    return st.as_dict()

@@ -53,3 +53,29 @@ def test_hamiltonian_two_vortex():
     """H = Gamma1 Gamma2 log(d) / (2 pi) for two bodies (both ordered pairs)."""
     x, G = W.two_vortex(2.5, 1.5, -0.7)
     assert qoi.hamiltonian(x, G) == pytest.approx(1.5 * -0.7 * np.log(2.5) / (2 * np.pi), rel=1e-14)
+
+
+def test_adjoint_of_linear_impulse_is_closed_form():
+    """P(T) = sum Gamma x(T) is conserved, so d/dx0 (P_chi + P_psi) = Gamma
+    for both components and d/dGamma (with Gamma also in L) = chi0 + psi0."""
+    x0, G = W.disk(24, seed=13)
+    n = G.size
+    lam_T = np.concatenate([G, G])
+    gx, gG, traj = fom.adjoint_rollout(x0, G, 0.05, 0.01, 8, lam_T)
+    np.testing.assert_allclose(gx, np.concatenate([G, G]), atol=1e-10)
+    gG_total = gG + traj[-1][:n] + traj[-1][n:]          # explicit d L / d Gamma
+    np.testing.assert_allclose(gG_total, x0[:n] + x0[n:], atol=1e-10)
+
+
+def test_adjoint_matches_finite_differences():
+    x0, G = W.disk(16, seed=14)
+    lam_T = W.random_vectors(x0.size, 1, seed=15)[0]
+    gx, gG, _ = fom.adjoint_rollout(x0, G, 0.05, 0.01, 6, lam_T)
+    dirs = W.random_vectors(x0.size + G.size, 4, seed=16)
+    h = 1e-5
+    for d in dirs:
+        dx, dg = d[:x0.size], d[x0.size:]
+        Lp = lam_T @ fom.rollout(x0 + h * dx, G + h * dg, 0.05, 0.01, 6, mode="dense", tol=1e-14)[0][-1]
+        Lm = lam_T @ fom.rollout(x0 - h * dx, G - h * dg, 0.05, 0.01, 6, mode="dense", tol=1e-14)[0][-1]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - (gx @ dx + gG @ dg)) <= 1e-7 * max(1.0, abs(fd))
