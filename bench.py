@@ -299,6 +299,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_ptrom:
         line["ptrom"] = ptrom_leg(ptrom, dev, ms_all / args.steps)
+    if rank == 0 and not args.no_batch:
+        line["batched"] = batch_leg(ptrom, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
@@ -398,6 +400,69 @@ def ptrom_leg(ptrom, dev, fom_ms_per_step, steps=200):
     return out
 
 
+def batch_leg(ptrom, dev):
+    """Batched FOM over 64 instances of uneven N (log-uniform in [4096,
+    131072], separation and circulation ratio uniform in their ranges, seed 3):
+    aggregate pair evals/s of one batched velocity launch and of one batched
+    block-diagonal Newton step, against per-instance launches."""
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    ns, seps, ratios = W.batch_instances(64, seed=3)
+    xs, Gs = [], []
+    for k, (n, sep, ratio) in enumerate(zip(ns, seps, ratios)):
+        x, G = W.two_cluster(int(n), seed=k, sep=float(sep), ratio=float(ratio))
+        xs.append(torch.tensor(x, device=dev))
+        Gs.append(torch.tensor(G, device=dev))
+    pairs = float(sum(int(n) * int(n) for n in ns))
+    deltas = [WORKLOAD["delta"]] * len(xs)
+    fs = [torch.empty_like(x) for x in xs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    t_b = timed(lambda: ptrom.bs_velocity_batched(xs, Gs, deltas, f_outs=fs), 3)
+    t_s = timed(lambda: [ptrom.bs_velocity(x, G, WORKLOAD["delta"], f_out=f) for x, G, f in zip(xs, Gs, fs)], 3)
+    p = ptrom.fom_params(WORKLOAD["dt"], WORKLOAD["delta"], "blockdiag", prec="fp32c")
+    works = [ptrom.fom_workspace(p, G.numel(), dev) for G in Gs]
+    xb = [x.clone() for x in xs]
+    fb = [ptrom.bs_velocity(x, G, WORKLOAD["delta"]) for x, G in zip(xb, Gs)]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    stats = ptrom.fom_step_batched(p, Gs, xb, fb, works)
+    torch.cuda.synchronize(dev)
+    tb_step = time.perf_counter() - t0
+    xsg = [x.clone() for x in xs]
+    fsg = [ptrom.bs_velocity(x, G, WORKLOAD["delta"]) for x, G in zip(xsg, Gs)]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    it_single = 0
+    for x, G, f, w in zip(xsg, Gs, fsg, works):
+        it_single += ptrom.fom_step(p, G, x, f, work=w)["velocity_evals"]
+    torch.cuda.synchronize(dev)
+    ts_step = time.perf_counter() - t0
+    evals_b = sum(s["velocity_evals"] * int(n) ** 2 for s, n in zip(stats, ns))
+    return {
+        "workload": "64 two-cluster instances, N log-uniform in [4096, 131072] (seed 3), delta 0.02, dt 0.005",
+        "total_bodies": int(sum(ns)), "pairs_per_velocity_eval": pairs,
+        "batched_velocity_ms": t_b, "per_instance_velocity_ms": t_s,
+        "batched_velocity_pairs_per_s": pairs / (t_b * 1e-3),
+        "per_instance_velocity_pairs_per_s": pairs / (t_s * 1e-3),
+        "batched_fom_step_s": tb_step, "per_instance_fom_step_s": ts_step,
+        "batched_fom_step_pairs_per_s": evals_b / tb_step,
+        "fom_mode": "block-diagonal inexact Newton (the paper's), FP32C pair sums",
+    }
+
+
 def _traffic(kind, n):
     """DRAM bytes per launch from the committed ncu capture of this kernel at
     this size; None when there is none or the kernel sources changed since."""
@@ -481,6 +546,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ptrom", action="store_true", help="skip the PTROM speed-up leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")

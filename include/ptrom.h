@@ -225,6 +225,29 @@ int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x,
              ptrom_stream_t stream);
 
 /*
+ * Batched FOM over B independent instances of uneven size (parameter sweeps):
+ * bs_velocity_batched evaluates Eq. 2 (optionally with the self blocks) for
+ * every instance in ONE pack launch and ONE all-pairs launch (a flattened
+ * work list of 64-target blocks).  fom_step_batched advances every instance
+ * by one trapezoid step with the paper's inexact block-diagonal Newton; each
+ * Newton iteration is one batched launch for the instances not yet converged.
+ * n, x, Gamma, f, selfjac_out, work, work_bytes: HOST arrays of length B
+ * holding per-instance sizes / DEVICE pointers / byte counts
+ * (work[b]: fom_workspace_bytes(p, n[b]) bytes, 256-byte aligned);
+ * delta: host array of per-instance constants (velocity); stats: optional
+ * host array of B.  fom_step_batched synchronises once per Newton iteration
+ * and requires p->jac_mode == PTROM_JAC_BLOCKDIAG.
+ */
+int bs_velocity_batched(int B, const int *n, const double *const *x,
+                        const double *const *Gamma, const double *delta,
+                        double *const *f_out, double *const *selfjac_out, int prec,
+                        ptrom_stream_t stream);
+int fom_step_batched(const ptrom_fom_params *p, int B, const int *n,
+                     const double *const *Gamma, double *const *x, double *const *f,
+                     void *const *work, const size_t *work_bytes,
+                     ptrom_fom_stats *stats, ptrom_stream_t stream);
+
+/*
  * fom_adjoint_step -- reverse-mode derivative of one fom_step (implicit
  * function theorem on the trapezoid residual r(x^n, x^{n-1}, Gamma) = 0 of
  * Eq. linKstep).  Given lambda = dL/dx^n:

@@ -11,6 +11,8 @@
 //   dGamma:    g_t += w_j . e3 x (s_j - t) r / (2 pi)
 // The difference forms make the j == t term vanish identically and avoid the
 // cancellation of D_t v_t against the off-diagonal sum.
+#include <vector>
+
 #include "internal.h"
 #include "pairsum.cuh"
 
@@ -342,9 +344,48 @@ int vjp(int n, const double *x, const double *G, double delta, const double *w, 
 }
 size_t pack_scratch_bytes(int ns) { return pack_scratch_bytes_impl(ns); }
 
+// Batched velocity over B instances (one pack + one cluster launch).
+template <typename R, bool WD, bool MASK>
+static int velocity_batched_impl(int B, const int *n, const double *const *x, const double *const *G,
+                                 const double *delta, double *const *f, double *const *D, cudaStream_t st, int S) {
+    using Op = VelOp<R, WD, MASK>;
+    std::vector<typename Op::Args> args(B);
+    for (int b = 0; b < B; ++b) args[b] = typename Op::Args{n[b], n[b], x[b], x[b], G[b], delta[b], f[b], WD ? D[b] : nullptr};
+    return launch_pairs_batched<Op>(args.data(), n, n, B, st, S);
+}
+
+int velocity_batched(int B, const int *n, const double *const *x, const double *const *G, const double *delta,
+                     double *const *f, double *const *D, int prec, cudaStream_t st, int S) {
+    bool any0 = false, withD = D != nullptr;
+    for (int b = 0; b < B; ++b) any0 = any0 || delta[b] == 0.0;
+    if (S <= 0) S = 1;
+    if (prec == PTROM_FP64) {
+        if (withD) return velocity_batched_impl<double, true, true>(B, n, x, G, delta, f, D, st, S);
+        if (any0) return velocity_batched_impl<double, false, true>(B, n, x, G, delta, f, D, st, S);
+        return velocity_batched_impl<double, false, false>(B, n, x, G, delta, f, D, st, S);
+    }
+    if (withD) return velocity_batched_impl<float, true, true>(B, n, x, G, delta, f, D, st, S);
+    if (any0) return velocity_batched_impl<float, false, true>(B, n, x, G, delta, f, D, st, S);
+    return velocity_batched_impl<float, false, false>(B, n, x, G, delta, f, D, st, S);
+}
+
 }  // namespace ptrom
 
 using namespace ptrom;
+
+extern "C" int bs_velocity_batched(int B, const int *n, const double *const *x, const double *const *Gamma,
+                                   const double *delta, double *const *f_out, double *const *selfjac_out, int prec,
+                                   ptrom_stream_t stream) {
+    if (B < 1 || !n || !x || !Gamma || !delta || !f_out)
+        return set_error(PTROM_EINVAL, "bs_velocity_batched: bad arguments");
+    if (prec != PTROM_FP32C && prec != PTROM_FP64) return set_error(PTROM_EINVAL, "bs_velocity_batched: bad prec");
+    for (int b = 0; b < B; ++b) {
+        if (n[b] < 1 || !x[b] || !Gamma[b] || !f_out[b] || !(delta[b] >= 0.0) || (selfjac_out && !selfjac_out[b]))
+            return set_error(PTROM_EINVAL, "bs_velocity_batched: bad instance %d", b);
+    }
+    const int S = g_source_split.load() > 0 ? g_source_split.load() : 2;
+    return velocity_batched(B, n, x, Gamma, delta, f_out, selfjac_out, prec, (cudaStream_t)stream, S);
+}
 
 extern "C" int bs_velocity(int nt, const double *xt, int ns, const double *xs, const double *Gamma,
                            double delta, double *f_out, double *selfjac_out, int prec,

@@ -714,3 +714,147 @@ extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *
     PTROM_CUDA(cudaGetLastError());
     return PTROM_OK;
 }
+
+
+// ---------------------------------------------------------------- batched FOM
+namespace ptrom {
+struct BInst {
+    int n;
+    double *x, *xprev, *fxi, *fprev, *r, *D;
+    Red red;
+    double *norm_out;  // [2]
+};
+
+__global__ void k_residual_batched(const BInst *__restrict__ I, double hdt) {
+    const BInst b = I[blockIdx.y];
+    __shared__ double sh[32];
+    const int n2 = 2 * b.n;
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+        const double v = b.x[i] - b.xprev[i] - hdt * (b.fxi[i] + b.fprev[i]);
+        b.r[i] = v;
+        s0 += v * v;
+        s1 += b.x[i] * b.x[i];
+    }
+    const double t0 = block_sum(s0, sh);
+    const double t1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) {
+        b.red.partials[blockIdx.x * 2 + 0] = t0;
+        b.red.partials[blockIdx.x * 2 + 1] = t1;
+    }
+    Red rr = b.red;
+    rr.out = b.norm_out;
+    finish_reduction(rr, 2);
+}
+
+__global__ void k_blockdiag_batched(const BInst *__restrict__ I, double hdt) {
+    const BInst b = I[blockIdx.y];
+    const int n = b.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d00 = b.D[i], d01 = b.D[n + i], d10 = b.D[2 * n + i], d11 = -d00;
+        const double m00 = 1.0 - hdt * d00, m01 = -hdt * d01, m10 = -hdt * d10, m11 = 1.0 - hdt * d11;
+        const double det = m00 * m11 - m01 * m10;
+        const double r0 = b.r[i], r1 = b.r[n + i];
+        b.x[i] -= (m11 * r0 - m01 * r1) / det;
+        b.x[n + i] -= (m00 * r1 - m10 * r0) / det;
+    }
+}
+}  // namespace ptrom
+
+extern "C" int fom_step_batched(const ptrom_fom_params *p, int B, const int *n, const double *const *Gamma,
+                                double *const *x, double *const *f, void *const *work, const size_t *work_bytes,
+                                ptrom_fom_stats *stats, ptrom_stream_t stream) {
+    using namespace ptrom;
+    if (!p || B < 1 || !n || !Gamma || !x || !f || !work || !work_bytes)
+        return set_error(PTROM_EINVAL, "fom_step_batched: bad arguments");
+    if (p->jac_mode != PTROM_JAC_BLOCKDIAG)
+        return set_error(PTROM_EINVAL, "fom_step_batched: only the block-diagonal (inexact) Jacobian is batched");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<Work> W(B);
+    for (int b = 0; b < B; ++b) {
+        PTROM_TRY(validate(p, n[b]));
+        if (!Gamma[b] || !x[b] || !f[b] || !work[b] || (((uintptr_t)work[b]) & 255))
+            return set_error(PTROM_EINVAL, "fom_step_batched: bad instance %d", b);
+        W[b] = layout(p, n[b], (char *)work[b]);
+        if (work_bytes[b] < W[b].bytes) return set_error(PTROM_EINVAL, "fom_step_batched: work %d too small", b);
+        PTROM_CUDA(cudaMemsetAsync(W[b].counter, 0, 64, st));
+        PTROM_CUDA(cudaMemcpyAsync(W[b].xprev, x[b], sizeof(double) * 2 * n[b], cudaMemcpyDeviceToDevice, st));
+        PTROM_CUDA(cudaMemcpyAsync(W[b].fprev, f[b], sizeof(double) * 2 * n[b], cudaMemcpyDeviceToDevice, st));
+        if (stats) memset(&stats[b], 0, sizeof(ptrom_fom_stats));
+    }
+    const double hdt = 0.5 * p->dt;
+    int maxn = 0;
+    for (int b = 0; b < B; ++b) maxn = std::max(maxn, n[b]);
+    const int rg = std::min(red_grid(2 * maxn), 2 * device_sm_count());
+    BInst *dinst = nullptr;
+    double *dnorm = nullptr;
+    PTROM_TRY(scratch_alloc((void **)&dinst, sizeof(BInst) * B, st));
+    PTROM_TRY(scratch_alloc((void **)&dnorm, sizeof(double) * 2 * B, st));
+    std::vector<int> active(B);
+    for (int b = 0; b < B; ++b) active[b] = b;
+    std::vector<double> norms(2 * B);
+    int status = PTROM_OK;
+    for (int k = 0; k <= p->max_iter && !active.empty(); ++k) {
+        const int A = (int)active.size();
+        std::vector<int> an(A);
+        std::vector<const double *> ax(A), aG(A);
+        std::vector<double> ad(A);
+        std::vector<double *> af(A), aD(A);
+        std::vector<BInst> hi(A);
+        for (int a = 0; a < A; ++a) {
+            const int b = active[a];
+            an[a] = n[b];
+            ax[a] = x[b];
+            aG[a] = Gamma[b];
+            ad[a] = p->delta;
+            af[a] = W[b].fxi;
+            aD[a] = W[b].D;
+            hi[a] = BInst{n[b], x[b], W[b].xprev, W[b].fxi, W[b].fprev, W[b].r, W[b].D,
+                          Red{W[b].partials, W[b].counter, W[b].redout}, dnorm + 2 * a};
+            if (stats) stats[b].velocity_evals++;
+        }
+        PTROM_TRY(velocity_batched(A, an.data(), ax.data(), aG.data(), ad.data(), af.data(), aD.data(), p->prec, st, 2));
+        PTROM_CUDA(cudaMemcpyAsync(dinst, hi.data(), sizeof(BInst) * A, cudaMemcpyHostToDevice, st));
+        k_residual_batched<<<dim3(rg, A), kRedThreads, 0, st>>>(dinst, hdt);
+        count_launch();
+        PTROM_CUDA(cudaMemcpyAsync(norms.data(), dnorm, sizeof(double) * 2 * A, cudaMemcpyDeviceToHost, st));
+        PTROM_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> next;
+        std::vector<BInst> upd;
+        for (int a = 0; a < A; ++a) {
+            const int b = active[a];
+            const double rn = sqrt(norms[2 * a]), xn = sqrt(norms[2 * a + 1]);
+            if (stats) {
+                if (k == 0) stats[b].res_norm0 = rn;
+                stats[b].res_norm = rn;
+            }
+            if (!isfinite(rn)) {
+                status = set_error(PTROM_ENAN, "fom_step_batched: non-finite residual in instance %d", b);
+                PTROM_CUDA(cudaMemcpyAsync(f[b], W[b].fxi, sizeof(double) * 2 * n[b], cudaMemcpyDeviceToDevice, st));
+                continue;
+            }
+            const bool conv = rn <= p->tol * (xn > 1.0 ? xn : 1.0);
+            if (conv || k == p->max_iter) {
+                PTROM_CUDA(cudaMemcpyAsync(f[b], W[b].fxi, sizeof(double) * 2 * n[b], cudaMemcpyDeviceToDevice, st));
+                if (!conv && status == PTROM_OK)
+                    status = set_error(PTROM_ENOCONV, "fom_step_batched: instance %d did not converge", b);
+                continue;
+            }
+            if (stats) stats[b].newton_iters++;
+            next.push_back(b);
+            upd.push_back(hi[a]);
+        }
+        if (!upd.empty()) {
+            PTROM_CUDA(cudaMemcpyAsync(dinst, upd.data(), sizeof(BInst) * upd.size(), cudaMemcpyHostToDevice, st));
+            k_blockdiag_batched<<<dim3(std::min(4 * device_sm_count(), (maxn + 255) / 256), (int)upd.size()), 256, 0, st>>>(
+                dinst, hdt);
+            count_launch();
+            PTROM_CUDA(cudaGetLastError());
+        }
+        active.swap(next);
+    }
+    PTROM_TRY(scratch_free(dinst, st));
+    PTROM_TRY(scratch_free(dnorm, st));
+    PTROM_CUDA(cudaStreamSynchronize(st));
+    return status;
+}

@@ -15,6 +15,9 @@ int jvp(int n, const double *x, const double *G, double delta, const double *v, 
 int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
         double *gG, int prec, cudaStream_t st, int split, void *scratch = nullptr);
 size_t pack_scratch_bytes(int ns);
+// Batched velocity (+ self blocks when D != nullptr) over B instances; S = source split.
+int velocity_batched(int B, const int *n, const double *const *x, const double *const *G, const double *delta,
+                     double *const *f, double *const *D, int prec, cudaStream_t st, int S);
 // J Phi (jphi.cu); split = source split over gridDim.z (0 = automatic).
 int jphi(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out, int prec,
          cudaStream_t st, int split);

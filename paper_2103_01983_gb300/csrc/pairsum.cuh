@@ -25,6 +25,9 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <string.h>
+
+#include <vector>
 
 #include "common.cuh"
 
@@ -112,9 +115,11 @@ pack_kernel(const typename Op::Args args, typename Op::Rec *__restrict__ out, in
         out[j] = Op::pack(args, j, org);
 }
 
+// One CTA's work: targets tbase .. tbase+63 against the sources of this
+// CTA's split (gridDim.y) of `nchunks` packed chunks.
 template <class Op>
-__global__ void __launch_bounds__(kThreads, Op::kMinBlocks)
-pair_kernel(const typename Op::Args args, const typename Op::Rec *__restrict__ packed, int nchunks) {
+__device__ __forceinline__ void pair_block(const typename Op::Args &args, const typename Op::Rec *__restrict__ packed,
+                                           int nchunks, int tbase) {
     using R = typename Op::Real;
     using V = typename VT<R>::V;
     using Rec = typename Op::Rec;
@@ -131,7 +136,6 @@ pair_kernel(const typename Op::Args args, const typename Op::Rec *__restrict__ p
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int tbase = blockIdx.x * kTB;
 
     const typename Op::Origin org = Op::origin(args);
     typename Op::Tgt tgt;
@@ -212,6 +216,52 @@ pair_kernel(const typename Op::Args args, const typename Op::Rec *__restrict__ p
     cluster.sync();
 }
 
+template <class Op>
+__global__ void __launch_bounds__(kThreads, Op::kMinBlocks)
+pair_kernel(const typename Op::Args args, const typename Op::Rec *__restrict__ packed, int nchunks) {
+    pair_block<Op>(args, packed, nchunks, blockIdx.x * kTB);
+}
+
+// Batched launch: instance b owns CTAs prefix[b] .. prefix[b+1]-1 along x.
+template <class Op>
+struct BatchItem {
+    typename Op::Args args;
+    const typename Op::Rec *packed;
+    int nchunks;
+};
+
+template <class Op>
+__global__ void __launch_bounds__(kThreads, Op::kMinBlocks)
+pair_kernel_batched(const BatchItem<Op> *__restrict__ items, const int *__restrict__ prefix, int B) {
+    int lo = 0, hi = B - 1;  // largest b with prefix[b] <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchItem<Op> it = items[lo];
+    pair_block<Op>(it.args, it.packed, it.nchunks, ((int)blockIdx.x - prefix[lo]) * kTB);
+}
+
+// Batched packing: record e of the flattened list belongs to the instance b
+// with rec_prefix[b] <= e < rec_prefix[b+1].
+template <class Op>
+__global__ void __launch_bounds__(256)
+pack_kernel_batched(const BatchItem<Op> *__restrict__ items, const int *__restrict__ rec_prefix, int B,
+                    typename Op::Rec *__restrict__ out) {
+    const int total = rec_prefix[B];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rec_prefix[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const typename Op::Args &a = items[lo].args;
+        out[e] = Op::pack(a, e - rec_prefix[lo], Op::origin(a));
+    }
+}
+
 // Launch helper: packs the sources (into `scratch` when given, else into a
 // stream-ordered allocation freed right after), picks the cluster split S
 // (1..8) that best fills the GPU's CTA slots, and launches the pair kernel.
@@ -276,6 +326,62 @@ int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t str
     if (e != cudaSuccess) return check_cuda(e, "pair_kernel launch");
     count_launch();
     return PTROM_OK;
+}
+
+// Batched launch over B instances: args[b], nt[b] targets, ns[b] sources.
+// One pack launch and one cluster launch (split S for every instance).
+template <class Op>
+int launch_pairs_batched(const typename Op::Args *args, const int *nt, const int *ns, int B, cudaStream_t stream,
+                         int S) {
+    using Rec = typename Op::Rec;
+    if (B < 1) return PTROM_OK;
+    if (S < 1 || S > kMaxCluster) return set_error(PTROM_EINVAL, "bad source split %d", S);
+    std::vector<BatchItem<Op>> items(B);
+    std::vector<int> prefix(B + 1, 0), rprefix(B + 1, 0);
+    for (int b = 0; b < B; ++b) {
+        const int nchunks = (ns[b] + kChunk - 1) / kChunk;
+        items[b].args = args[b];
+        items[b].nchunks = nchunks;
+        prefix[b + 1] = prefix[b] + (nt[b] + kTB - 1) / kTB;
+        rprefix[b + 1] = rprefix[b] + nchunks * kChunk;
+    }
+    const size_t head = ((sizeof(BatchItem<Op>) * B + 2 * sizeof(int) * (B + 1)) + 255) & ~size_t(255);
+    char *buf = nullptr;
+    PTROM_TRY(scratch_alloc((void **)&buf, head + sizeof(Rec) * (size_t)rprefix[B], stream));
+    Rec *packed = reinterpret_cast<Rec *>(buf + head);
+    for (int b = 0; b < B; ++b) items[b].packed = packed + rprefix[b];
+    BatchItem<Op> *ditems = reinterpret_cast<BatchItem<Op> *>(buf);
+    int *dprefix = reinterpret_cast<int *>(buf + sizeof(BatchItem<Op>) * B);
+    int *drprefix = dprefix + (B + 1);
+    std::vector<char> hostbuf(head);
+    memcpy(hostbuf.data(), items.data(), sizeof(BatchItem<Op>) * B);
+    memcpy(hostbuf.data() + sizeof(BatchItem<Op>) * B, prefix.data(), sizeof(int) * (B + 1));
+    memcpy(hostbuf.data() + sizeof(BatchItem<Op>) * B + sizeof(int) * (B + 1), rprefix.data(), sizeof(int) * (B + 1));
+    cudaError_t e = cudaMemcpyAsync(buf, hostbuf.data(), head, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) {
+        int pgrid = (rprefix[B] + 255) / 256;
+        if (pgrid > 8 * device_sm_count()) pgrid = 8 * device_sm_count();
+        pack_kernel_batched<Op><<<pgrid, 256, 0, stream>>>(ditems, drprefix, B, packed);
+        count_launch();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(prefix[B], S, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1;
+        attr[0].val.clusterDim.y = S;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const int slot = timing_begin(Op::kKind, stream);
+        e = cudaLaunchKernelEx(&cfg, pair_kernel_batched<Op>, (const BatchItem<Op> *)ditems, (const int *)dprefix, B);
+        timing_end(slot, stream);
+        if (e == cudaSuccess) count_launch();
+    }
+    const int s2 = scratch_free(buf, stream);
+    if (e != cudaSuccess) return check_cuda(e, "pair_kernel_batched launch");
+    return s2;
 }
 
 // Bytes of packed-source scratch one launch over ns sources needs (upper

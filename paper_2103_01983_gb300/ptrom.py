@@ -131,6 +131,9 @@ def _load():
         "fom_adjoint_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
         "fom_adjoint_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                               ctypes.POINTER(FomStats), _vp], _i),
+        "bs_velocity_batched": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
+        "fom_step_batched": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, _vp, _vp,
+                              ctypes.POINTER(FomStats), _vp], _i),
         "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
         "fom_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                       ctypes.POINTER(FomStats), _vp], _i),
@@ -419,3 +422,32 @@ def fom_adjoint_step(params, Gamma, x_n, x_prev, lam, gGamma, work=None, stream=
                                 _ptr(gGamma), ctypes.c_void_p(work.data_ptr()), work.numel(), ctypes.byref(st),
                                 _stream(stream)))
     return st.as_dict()
+
+
+def _ptr_array(ts):
+    return (_vp * len(ts))(*[ctypes.c_void_p(t.data_ptr()) for t in ts])
+
+
+def bs_velocity_batched(xs, Gammas, deltas, f_outs=None, selfjac=False, prec="fp32c", stream=None):
+    """Velocity of B instances (lists of per-instance tensors) in one launch."""
+    B = len(xs)
+    n = (_i * B)(*[g.numel() for g in Gammas])
+    if f_outs is None:
+        f_outs = [torch.empty_like(x) for x in xs]
+    Ds = [torch.empty(3 * g.numel(), dtype=torch.float64, device=g.device) for g in Gammas] if selfjac else None
+    d = (_d * B)(*[float(v) for v in deltas])
+    _check(lib.bs_velocity_batched(B, n, _ptr_array(xs), _ptr_array(Gammas), d, _ptr_array(f_outs),
+                                   _ptr_array(Ds) if selfjac else None, _prec(prec), _stream(stream)))
+    return (f_outs, Ds) if selfjac else f_outs
+
+
+def fom_step_batched(params, Gammas, xs, fs, works, stream=None):
+    """One block-diagonal Newton trapezoid step for B instances (in place)."""
+    B = len(xs)
+    n = (_i * B)(*[g.numel() for g in Gammas])
+    wb = (ctypes.c_size_t * B)(*[w.numel() for w in works])
+    st = (FomStats * B)()
+    status = lib.fom_step_batched(ctypes.byref(params), B, n, _ptr_array(Gammas), _ptr_array(xs),
+                                  _ptr_array(fs), _ptr_array(works), wb, st, _stream(stream))
+    _check(status)
+    return [s.as_dict() for s in st]
