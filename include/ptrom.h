@@ -408,6 +408,27 @@ int ptrom_reconstruct(const ptrom_model *m, const double *xhat, const int *rows,
 int ptrom_model_query(const ptrom_model *m, int *n, int *M, int *M_r, int *n_s,
                       int *N_c, double *phi, double *sigma, int *sampled, double *A);
 
+/* ------------------------------------------------------------------------
+ * ptrom_save / ptrom_load -- a model as one binary file, so the offline
+ * stages of Sec. 5.1 run once and the online model of Sec. 5.2-5.3 is
+ * reloaded without retraining.
+ *   ptrom_save  writes every array the model was created or last
+ *               reparametrised with (FP64 host copies, not the FP32 device
+ *               forms), plus, for models made by ptrom_build, the basis,
+ *               singular values, sampled bodies, cluster memberships and the
+ *               current x^0; the file ends with a 64-bit FNV-1a hash.
+ *   ptrom_load  reads such a file and creates the model on the current
+ *               device (as ptrom_model_create would); the caller owns *out
+ *               and releases it with ptrom_free.  A loaded model steps,
+ *               reparametrises and reconstructs exactly as the saved one.
+ * Errors: PTROM_EINVAL for NULL arguments, files that cannot be opened or
+ * written, a wrong tag, byte order or format version, a failed hash, array
+ * lengths that disagree with the sizes, or out-of-range indices; PTROM_ECUDA
+ * / PTROM_ENOMEM from the device upload.  On error *out is NULL.
+ * ------------------------------------------------------------------------ */
+int ptrom_save(const ptrom_model *m, const char *path);
+int ptrom_load(const char *path, ptrom_model **out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -127,6 +127,8 @@ struct JvpOp {
         const double *x, *G, *v;
         double delta;
         double *jv;
+        const double *lz;  // optional: jv := lz - lhdt * (J v)
+        double lhdt;
     };
     struct __align__(16) Rec { V nx, ny, nvx, nvy, g; };
     struct Tgt { V x, y, vx, vy, dd; };
@@ -180,8 +182,13 @@ struct JvpOp {
         p[3] = T2::fma(a, m, p[3]);                     // sum a m
     }
     static __device__ __forceinline__ void finalize(const Args &a, int t, const double *s) {
-        a.jv[t] = 2.0 * s[0] - s[1];
-        a.jv[a.n + t] = s[2] - 2.0 * s[3];
+        double o0 = 2.0 * s[0] - s[1], o1 = s[2] - 2.0 * s[3];
+        if (a.lz) {
+            o0 = a.lz[t] - a.lhdt * o0;
+            o1 = a.lz[a.n + t] - a.lhdt * o1;
+        }
+        a.jv[t] = o0;
+        a.jv[a.n + t] = o1;
     }
 };
 
@@ -200,6 +207,8 @@ struct VjpOp {
         const double *x, *G, *w;
         double delta;
         double *gx, *gG;
+        const double *lz;  // optional: gx := lz - lhdt * (J^T w)
+        double lhdt;
     };
     struct __align__(16) Rec { V nx, ny, wx, nwy, g; };
     struct Tgt { V x, y, wx, wy, g, ng, dd; };
@@ -263,8 +272,13 @@ struct VjpOp {
     }
     static __device__ __forceinline__ void finalize(const Args &a, int t, const double *s) {
         if (GX) {
-            a.gx[t] = s[0] + 2.0 * s[1];
-            a.gx[a.n + t] = -s[2] + 2.0 * s[3];
+            double o0 = s[0] + 2.0 * s[1], o1 = -s[2] + 2.0 * s[3];
+            if (a.lz) {
+                o0 = a.lz[t] - a.lhdt * o0;
+                o1 = a.lz[a.n + t] - a.lhdt * o1;
+            }
+            a.gx[t] = o0;
+            a.gx[a.n + t] = o1;
         }
         if (GG) a.gG[t] = s[GX ? 4 : 0] * kInv2Pi;
     }
@@ -288,35 +302,35 @@ static int velocity_impl(int nt, const double *xt, int ns, const double *xs, con
 
 template <typename R>
 static int jvp_impl(int n, const double *x, const double *G, double delta, const double *v,
-                    double *jv, cudaStream_t st, int split, void *scr) {
+                    double *jv, cudaStream_t st, int split, void *scr, LinEpi lin) {
     if (delta == 0.0) {
-        typename JvpOp<R, true>::Args a{n, x, G, v, delta, jv};
+        typename JvpOp<R, true>::Args a{n, x, G, v, delta, jv, lin.z, lin.hdt};
         return launch_pairs<JvpOp<R, true>>(a, n, n, st, split, scr);
     }
-    typename JvpOp<R, false>::Args a{n, x, G, v, delta, jv};
+    typename JvpOp<R, false>::Args a{n, x, G, v, delta, jv, lin.z, lin.hdt};
     return launch_pairs<JvpOp<R, false>>(a, n, n, st, split, scr);
 }
 
 template <typename R, bool MASK>
 static int vjp_impl2(int n, const double *x, const double *G, double delta, const double *w,
-                     double *gx, double *gG, cudaStream_t st, int split, void *scr) {
+                     double *gx, double *gG, cudaStream_t st, int split, void *scr, LinEpi lin) {
     if (gx && gG) {
-        typename VjpOp<R, MASK, true, true>::Args a{n, x, G, w, delta, gx, gG};
+        typename VjpOp<R, MASK, true, true>::Args a{n, x, G, w, delta, gx, gG, lin.z, lin.hdt};
         return launch_pairs<VjpOp<R, MASK, true, true>>(a, n, n, st, split, scr);
     }
     if (gx) {
-        typename VjpOp<R, MASK, true, false>::Args a{n, x, G, w, delta, gx, gG};
+        typename VjpOp<R, MASK, true, false>::Args a{n, x, G, w, delta, gx, gG, lin.z, lin.hdt};
         return launch_pairs<VjpOp<R, MASK, true, false>>(a, n, n, st, split, scr);
     }
-    typename VjpOp<R, MASK, false, true>::Args a{n, x, G, w, delta, gx, gG};
+    typename VjpOp<R, MASK, false, true>::Args a{n, x, G, w, delta, gx, gG, nullptr, 0.0};
     return launch_pairs<VjpOp<R, MASK, false, true>>(a, n, n, st, split, scr);
 }
 
 template <typename R>
 static int vjp_impl(int n, const double *x, const double *G, double delta, const double *w,
-                    double *gx, double *gG, cudaStream_t st, int split, void *scr) {
-    if (delta == 0.0) return vjp_impl2<R, true>(n, x, G, delta, w, gx, gG, st, split, scr);
-    return vjp_impl2<R, false>(n, x, G, delta, w, gx, gG, st, split, scr);
+                    double *gx, double *gG, cudaStream_t st, int split, void *scr, LinEpi lin) {
+    if (delta == 0.0) return vjp_impl2<R, true>(n, x, G, delta, w, gx, gG, st, split, scr, lin);
+    return vjp_impl2<R, false>(n, x, G, delta, w, gx, gG, st, split, scr, lin);
 }
 
 static int check_common(const char *fn, int nt, int ns, double delta, int prec) {
@@ -333,14 +347,14 @@ int velocity(int nt, const double *xt, int ns, const double *xs, const double *G
                               : velocity_impl<float>(nt, xt, ns, xs, G, delta, f, D, st, split, scr);
 }
 int jvp(int n, const double *x, const double *G, double delta, const double *v, double *jv,
-        int prec, cudaStream_t st, int split, void *scr) {
-    return prec == PTROM_FP64 ? jvp_impl<double>(n, x, G, delta, v, jv, st, split, scr)
-                              : jvp_impl<float>(n, x, G, delta, v, jv, st, split, scr);
+        int prec, cudaStream_t st, int split, void *scr, LinEpi lin) {
+    return prec == PTROM_FP64 ? jvp_impl<double>(n, x, G, delta, v, jv, st, split, scr, lin)
+                              : jvp_impl<float>(n, x, G, delta, v, jv, st, split, scr, lin);
 }
 int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
-        double *gG, int prec, cudaStream_t st, int split, void *scr) {
-    return prec == PTROM_FP64 ? vjp_impl<double>(n, x, G, delta, w, gx, gG, st, split, scr)
-                              : vjp_impl<float>(n, x, G, delta, w, gx, gG, st, split, scr);
+        double *gG, int prec, cudaStream_t st, int split, void *scr, LinEpi lin) {
+    return prec == PTROM_FP64 ? vjp_impl<double>(n, x, G, delta, w, gx, gG, st, split, scr, lin)
+                              : vjp_impl<float>(n, x, G, delta, w, gx, gG, st, split, scr, lin);
 }
 size_t pack_scratch_bytes(int ns) { return pack_scratch_bytes_impl(ns); }
 

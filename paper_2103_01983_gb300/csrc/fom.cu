@@ -9,7 +9,12 @@
 //   block-diagonal : per-body 2x2 solve with (I - dt/2 D_i)
 //   JFNK           : restarted right-preconditioned GMRES with classical
 //                    Gram-Schmidt applied twice (CGS2) on the device; the
-//                    (m+1) x m Hessenberg least-squares (Givens) on the host
+//                    (m+1) x m Hessenberg least-squares (Givens) on the host.
+//                    One Arnoldi step is three launches and one host read:
+//                    normalise + precondition, the J v pair kernel with the
+//                    (I - dt/2 J) epilogue, and CGS2 as one cooperative
+//                    kernel (three grid barriers); the correction
+//                    d = M^{-1} V y is one more launch per cycle.
 //   dense          : FP64 assembly of I - dt/2 J, LU with partial pivoting in
 //                    one cooperative kernel (one grid barrier per column),
 //                    forward/back substitution in one CTA.
@@ -149,33 +154,25 @@ __global__ void k_orth_update(int n2, int K, const double *V, const double *h, d
     finish_reduction(red, 1);
 }
 
-// y = alpha * x
-__global__ void k_scale(int n2, const double *x, double alpha, double *y) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) y[i] = alpha * x[i];
+// Per-body 2x2 solve (I - hdt D_i)^{-1} (r0, r1) (transposed block when
+// transpose is set); D = [D00 | D01 | D10], D11 = -D00.
+__device__ __forceinline__ void bd_solve(const double *D, int n, int i, double hdt, int transpose, double r0,
+                                         double r1, double scale, double &z0, double &z1) {
+    const double d00 = D[i], d11 = -d00;
+    const double d01 = transpose ? D[2 * n + i] : D[n + i], d10 = transpose ? D[n + i] : D[2 * n + i];
+    const double m00 = 1.0 - hdt * d00, m01 = -hdt * d01, m10 = -hdt * d10, m11 = 1.0 - hdt * d11;
+    const double det = m00 * m11 - m01 * m10;
+    z0 = scale * (m11 * r0 - m01 * r1) / det;
+    z1 = scale * (m00 * r1 - m10 * r0) / det;
 }
 
-// u = sum_k y[k] V_k   (y is a device array of K coefficients)
-__global__ void k_combine(int n2, int K, const double *V, const double *y, double *u) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s += y[k] * V[(size_t)k * n2 + i];
-        u[i] = s;
-    }
-}
-
-// Block-diagonal solve: z_i = scale * (I - hdt D_i)^{-1} v_i (transposed
-// blocks when transpose is set), added to z when accumulate is set.
-// D = [D00 | D01 | D10], D11 = -D00.
+// Block-diagonal solve: z_i = scale * (I - hdt D_i)^{-1} v_i, added to z
+// when accumulate is set.
 __global__ void k_blockdiag(int n, const double *D, const double *v, double hdt, double scale,
                             double *z, int accumulate, int transpose) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double d00 = D[i], d11 = -d00;
-        const double d01 = transpose ? D[2 * n + i] : D[n + i], d10 = transpose ? D[n + i] : D[2 * n + i];
-        const double m00 = 1.0 - hdt * d00, m01 = -hdt * d01, m10 = -hdt * d10, m11 = 1.0 - hdt * d11;
-        const double det = m00 * m11 - m01 * m10;
-        const double r0 = v[i], r1 = v[n + i];
-        const double z0 = scale * (m11 * r0 - m01 * r1) / det;
-        const double z1 = scale * (m00 * r1 - m10 * r0) / det;
+        double z0, z1;
+        bd_solve(D, n, i, hdt, transpose, v[i], v[n + i], scale, z0, z1);
         if (accumulate) {
             z[i] += z0;
             z[n + i] += z1;
@@ -186,17 +183,143 @@ __global__ void k_blockdiag(int n, const double *D, const double *v, double hdt,
     }
 }
 
-// w = z - hdt * jz
-__global__ void k_lin_op(int n2, const double *z, const double *jz, double hdt, double *w) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x)
-        w[i] = z[i] - hdt * jz[i];
+// Next Arnoldi vector and its preconditioned image in one pass:
+//   v = scale * src / (|scale| sqrt(*nrm2))  -> V_out,   z = M^{-1} v
+// (*nrm2 = ||src||^2 on the device, so the host need not read it first).
+__global__ void k_norm_precond(int n, const double *src, double scale, const double *nrm2, const double *D,
+                               double hdt, int transpose, double *V_out, double *z) {
+    const double inv = 1.0 / (fabs(scale) * sqrt(*nrm2));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v0 = inv * (scale * src[i]), v1 = inv * (scale * src[n + i]);
+        V_out[i] = v0;
+        V_out[n + i] = v1;
+        double z0, z1;
+        bd_solve(D, n, i, hdt, transpose, v0, v1, 1.0, z0, z1);
+        z[i] = z0;
+        z[n + i] = z1;
+    }
 }
 
-// r0 = b - (d - hdt * jd)
-__global__ void k_restart_res(int n2, const double *b, const double *d, const double *jd, double hdt,
-                              double *r0) {
+// GMRES correction of one cycle: d += M^{-1} (sum_k y_k V_k); with x given,
+// also x += d (the Newton update after the last cycle).
+struct Coef {
+    double y[kMaxRestart];
+};
+__global__ void k_combine_precond(int n, int K, const double *V, Coef c, const double *D, double hdt, int transpose,
+                                  double *d, double *x) {
+    const size_t n2 = 2 * (size_t)n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double u0 = 0.0, u1 = 0.0;
+        for (int k = 0; k < K; ++k) {
+            u0 += c.y[k] * V[k * n2 + i];
+            u1 += c.y[k] * V[k * n2 + n + i];
+        }
+        double z0, z1;
+        bd_solve(D, n, i, hdt, transpose, u0, u1, 1.0, z0, z1);
+        const double d0 = d[i] + z0, d1 = d[n + i] + z1;
+        d[i] = d0;
+        d[n + i] = d1;
+        if (x) {
+            x[i] += d0;
+            x[n + i] += d1;
+        }
+    }
+}
+
+// r0 = scale * rhs - a   (a = (I - hdt J) d)
+__global__ void k_restart_res(int n2, const double *rhs, double scale, const double *a, double *r0) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x)
-        r0[i] = b[i] - (d[i] - hdt * jd[i]);
+        r0[i] = scale * rhs[i] - a[i];
+}
+
+// Classical Gram-Schmidt applied twice to w against V_0..V_{K-1}, as one
+// cooperative kernel: each thread keeps its (at most kMaxPer) entries of w in
+// registers through both passes.  Per pass: block partial dots -> grid
+// barrier -> every block sums the partials in the same fixed order (so all
+// blocks hold identical coefficients) -> w -= sum_k h_k V_k.  Outputs:
+// out[0..K) = first-pass h, out[kMaxDots..) = second-pass h,
+// out[2 kMaxDots] = ||w||^2 after both passes; w is written back.
+// partials: 2 * gridDim.x * kMaxDots + gridDim.x doubles.
+__global__ void __launch_bounds__(kRedThreads)
+k_cgs2(int n2, int K, const double *V, double *w, double *partials, double *out) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sh[kRedThreads / 32][kMaxDots];
+    __shared__ double hs[kMaxDots];
+    const int G = gridDim.x;
+    const int stride = G * blockDim.x;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double wl[kMaxPer];
+#pragma unroll
+    for (int e = 0; e < kMaxPer; ++e) {
+        const int i = i0 + e * stride;
+        wl[e] = i < n2 ? w[i] : 0.0;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        double *P = partials + (size_t)pass * G * kMaxDots;
+        for (int k = 0; k < K; ++k) {
+            const double *vk = V + (size_t)k * n2;
+            double s = 0.0;
+#pragma unroll
+            for (int e = 0; e < kMaxPer; ++e) {
+                const int i = i0 + e * stride;
+                if (i < n2) s += vk[i] * wl[e];
+            }
+            s = warp_sum(s);
+            if (lane == 0) sh[warp][k] = s;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            double s = 0.0;
+            for (int q = 0; q < nw; ++q) s += sh[q][k];
+            P[(size_t)blockIdx.x * K + k] = s;
+        }
+        grid.sync();
+        for (int k = warp; k < K; k += nw) {
+            double s = 0.0;
+            for (int b = lane; b < G; b += 32) s += P[(size_t)b * K + k];
+            s = warp_sum(s);
+            if (lane == 0) hs[k] = s;
+        }
+        __syncthreads();
+        if (blockIdx.x == 0)
+            for (int k = threadIdx.x; k < K; k += blockDim.x) out[pass * kMaxDots + k] = hs[k];
+#pragma unroll
+        for (int e = 0; e < kMaxPer; ++e) {
+            const int i = i0 + e * stride;
+            if (i < n2) {
+                double v = wl[e];
+                for (int k = 0; k < K; ++k) v -= hs[k] * V[(size_t)k * n2 + i];
+                wl[e] = v;
+            }
+        }
+        __syncthreads();  // sh and hs are rewritten by the next pass
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int e = 0; e < kMaxPer; ++e) {
+        const int i = i0 + e * stride;
+        if (i < n2) {
+            w[i] = wl[e];
+            s += wl[e] * wl[e];
+        }
+    }
+    s = warp_sum(s);
+    if (lane == 0) sh[warp][0] = s;
+    __syncthreads();
+    double *Pn = partials + (size_t)2 * G * kMaxDots;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += sh[q][0];
+        Pn[blockIdx.x] = t;
+    }
+    grid.sync();
+    if (blockIdx.x == 0 && warp == 0) {
+        double t = 0.0;
+        for (int b = lane; b < G; b += 32) t += Pn[b];
+        t = warp_sum(t);
+        if (lane == 0) out[2 * kMaxDots] = t;
+    }
 }
 
 // y += a * x
@@ -318,7 +441,7 @@ __global__ void k_lu_solve(int m, const double *A, const int *perm, const double
 
 // ---------------------------------------------------------------- workspace
 struct Work {
-    double *xprev, *fprev, *fxi, *r, *D, *d, *jz, *w, *z, *b, *V, *partials, *redout, *ydev, *M;
+    double *xprev, *fprev, *fxi, *r, *D, *d, *jz, *w, *z, *b, *V, *partials, *redout, *M;
     void *pack;
     unsigned int *counter;
     int *perm, *status;
@@ -357,9 +480,10 @@ static Work layout(const ptrom_fom_params *p, int n, char *base) {
     W.b = (double *)take(n2 * 8);
     const int m = (p->jac_mode == PTROM_JAC_JFNK) ? p->gmres_restart : 0;
     W.V = (double *)take((size_t)(m + 1) * n2 * 8);
-    W.partials = (double *)take((size_t)2 * device_sm_count() * kMaxDots * 8);
+    // reductions: per-block partials, 2 passes of dots + 1 norm (k_cgs2)
+    const int rg = std::max(red_grid((int)n2), 2 * device_sm_count());
+    W.partials = (double *)take(((size_t)2 * rg * kMaxDots + rg) * 8);
     W.redout = (double *)take(4 * kMaxDots * 8);
-    W.ydev = (double *)take(kMaxDots * 8);
     W.counter = (unsigned int *)take(64);
     W.pack = take(pack_scratch_bytes(n));
     if (p->jac_mode == PTROM_JAC_DENSE) {
@@ -404,8 +528,20 @@ struct Ctx {
     cudaStream_t st;
     Work W;
     int grid, rgrid;
+    bool coop = false;  // CGS2 as one cooperative kernel (rgrid blocks co-resident)
     ptrom_fom_stats *stats;
 };
+
+// Whether `blocks` CTAs of k_cgs2 fit on the device at once.
+static bool cgs2_coop_fits(int blocks) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_cgs2, kRedThreads, 0) != cudaSuccess) v = 0;
+        per_sm = v;
+    }
+    return blocks <= per_sm * device_sm_count();
+}
 
 static Red mkred(const Work &W, int slot) { return Red{W.partials, W.counter, W.redout + slot * kMaxDots}; }
 
@@ -415,67 +551,91 @@ static int fetch(const Ctx &c, const double *dev, double *host, int count) {
     return PTROM_OK;
 }
 
-// A y = (I - hdt J) y through the all-pairs J v kernel.
-static int apply_jvp(Ctx &c, const double *v, double *out) {
+// out = J v, or with lin set out = (I - hdt J) v, through the all-pairs
+// J v kernel (J^T w for the adjoint solves).
+static int apply_jvp(Ctx &c, const double *v, double *out, bool lin) {
+    LinEpi L;
+    if (lin) {
+        L.z = v;
+        L.hdt = c.hdt;
+    }
     if (c.transpose) {
-        PTROM_TRY(vjp(c.n, c.xi, c.G, c.p->delta, v, out, nullptr, c.p->prec, c.st, 0, c.W.pack));
+        PTROM_TRY(vjp(c.n, c.xi, c.G, c.p->delta, v, out, nullptr, c.p->prec, c.st, 0, c.W.pack, L));
     } else {
-        PTROM_TRY(jvp(c.n, c.xi, c.G, c.p->delta, v, out, c.p->prec, c.st, 0, c.W.pack));
+        PTROM_TRY(jvp(c.n, c.xi, c.G, c.p->delta, v, out, c.p->prec, c.st, 0, c.W.pack, L));
     }
     if (c.stats) c.stats->jvp_evals++;
     return PTROM_OK;
 }
 
-// Solve (I - hdt J) d = rhs_scale * rhs with right-preconditioned GMRES(m).
-static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d) {
+// CGS2 of W.w against V_0..V_{K-1}: first-pass h at redout slot 1, second-pass
+// h at slot 2, ||w||^2 at slot 3 (one cooperative launch, or four launches
+// when the grid cannot be co-resident).
+static int cgs2(Ctx &c, int K) {
+    Work &W = c.W;
+    int n2 = c.n2;
+    if (c.coop) {
+        const double *V = W.V;
+        double *w = W.w, *P = W.partials, *out = W.redout + kMaxDots;
+        void *args[] = {&n2, &K, &V, &w, &P, &out};
+        PTROM_CUDA(cudaLaunchCooperativeKernel((void *)k_cgs2, dim3(c.rgrid), dim3(kRedThreads), args, 0, c.st));
+        count_launch();
+        return PTROM_OK;
+    }
+    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.w, mkred(W, 1));
+    k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.redout + kMaxDots, W.w, mkred(W, 3));
+    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.w, mkred(W, 2));
+    k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.redout + 2 * kMaxDots, W.w, mkred(W, 3));
+    count_launch(4);
+    PTROM_CUDA(cudaGetLastError());
+    return PTROM_OK;
+}
+
+// Solve (I - hdt J) d = rhs_scale * rhs with right-preconditioned GMRES(m),
+// M = blockdiag(I - hdt D_i).  rhs_nrm2: device address of ||rhs||^2 when the
+// caller has it (host value rhs_nrm2_host), else nullptr.  With x_upd given,
+// x_upd += d at the end (the Newton update).
+static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d, double *x_upd,
+                 const double *rhs_nrm2 = nullptr, double rhs_nrm2_host = 0.0) {
     const int n2 = c.n2, m = c.p->gmres_restart;
     Work &W = c.W;
     PTROM_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n2, c.st));
-    k_scale<<<c.grid, 256, 0, c.st>>>(n2, rhs, rhs_scale, W.b);
-    count_launch();
-    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, W.b, mkred(W, 0));
-    count_launch();
-    double bn2 = 0.0;
-    PTROM_TRY(fetch(c, W.redout, &bn2, 1));
-    const double bnorm = sqrt(bn2);
+    if (!rhs_nrm2) {
+        k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, rhs, mkred(W, 0));
+        count_launch();
+        PTROM_TRY(fetch(c, W.redout, &rhs_nrm2_host, 1));
+        rhs_nrm2 = W.redout;
+    }
+    const double bnorm = fabs(rhs_scale) * sqrt(rhs_nrm2_host);
     if (bnorm == 0.0) return PTROM_OK;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hbuf(3 * kMaxDots);
+    double *hdev = W.redout + kMaxDots;  // slots 1..3: h (two passes), ||w||^2
     int total = 0;
-    const double *r0 = W.b;  // first cycle: r0 = b (d = 0)
+    const double *r0 = rhs;  // first cycle: r0 = b (d = 0)
+    double r0_scale = rhs_scale;
+    const double *r0_nrm2 = rhs_nrm2;
     double beta = bnorm;
     while (true) {
-        k_scale<<<c.grid, 256, 0, c.st>>>(n2, r0, 1.0 / beta, W.V);
-        count_launch();
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int jl = -1;
         bool done = false;
         for (int j = 0; j < m; ++j) {
             double *vj = W.V + (size_t)j * n2;
-            k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, vj, c.hdt, 1.0, W.z, 0, c.transpose);
+            // v_j = previous Krylov vector / its norm (read on the device); z = M^{-1} v_j
+            if (j == 0)
+                k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, r0, r0_scale, r0_nrm2, W.D, c.hdt, c.transpose, vj, W.z);
+            else
+                k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, W.w, 1.0, hdev + 2 * kMaxDots, W.D, c.hdt, c.transpose,
+                                                          vj, W.z);
             count_launch();
-            PTROM_TRY(apply_jvp(c, W.z, W.jz));
-            k_lin_op<<<c.grid, 256, 0, c.st>>>(n2, W.z, W.jz, c.hdt, W.w);
-            count_launch();
-            // CGS2
-            k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.w, mkred(W, 0));
-            count_launch();
-            k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.redout, W.w, mkred(W, 2));
-            count_launch();
-            k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.w, mkred(W, 1));
-            count_launch();
-            k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, j + 1, W.V, W.redout + kMaxDots, W.w, mkred(W, 2));
-            count_launch();
-            PTROM_CUDA(cudaGetLastError());
-            PTROM_TRY(fetch(c, W.redout, hbuf.data(), 3 * kMaxDots));
+            PTROM_TRY(apply_jvp(c, W.z, W.w, true));  // w = (I - hdt J) z
+            PTROM_TRY(cgs2(c, j + 1));
+            PTROM_TRY(fetch(c, hdev, hbuf.data(), 2 * kMaxDots + 1));
             for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hbuf[i] + hbuf[kMaxDots + i];
             const double hn = sqrt(hbuf[2 * kMaxDots]);
             H[(size_t)(j + 1) * m + j] = hn;
             if (!isfinite(hn)) return set_error(PTROM_ENAN, "fom: non-finite Krylov vector");
-            if (hn > 0.0) {
-                k_scale<<<c.grid, 256, 0, c.st>>>(n2, W.w, 1.0 / hn, W.V + (size_t)(j + 1) * n2);
-                count_launch();
-            }
             // Givens
             for (int i = 0; i < j; ++i) {
                 const double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
@@ -498,33 +658,39 @@ static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d) {
                 break;
             }
         }
-        // y = R^{-1} g, d += M^{-1} V y
+        // y = R^{-1} g;  d += M^{-1} V y  (and x += d after the last cycle)
         const int K = jl + 1;
         for (int i = K - 1; i >= 0; --i) {
             double s = g[i];
             for (int k = i + 1; k < K; ++k) s -= H[(size_t)i * m + k] * y[k];
             y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
         }
-        PTROM_CUDA(cudaMemcpyAsync(W.ydev, y.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c.st));
-        k_combine<<<c.grid, 256, 0, c.st>>>(n2, K, W.V, W.ydev, W.w);
-        count_launch();
-        k_blockdiag<<<c.grid, 256, 0, c.st>>>(c.n, W.D, W.w, c.hdt, 1.0, d, 1, c.transpose);
+        Coef cf{};
+        for (int k = 0; k < K; ++k) cf.y[k] = y[k];
+        k_combine_precond<<<c.grid, 256, 0, c.st>>>(c.n, K, W.V, cf, W.D, c.hdt, c.transpose, d,
+                                                     done ? x_upd : nullptr);
         count_launch();
         PTROM_CUDA(cudaGetLastError());
         if (done) break;
-        // restart: r0 = b - A d
-        PTROM_TRY(apply_jvp(c, d, W.jz));
-        k_restart_res<<<c.grid, 256, 0, c.st>>>(n2, W.b, d, W.jz, c.hdt, W.z);
-        count_launch();
-        k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, W.z, mkred(W, 0));
-        count_launch();
+        // restart: r0 = b - (I - hdt J) d
+        PTROM_TRY(apply_jvp(c, d, W.jz, true));
+        k_restart_res<<<c.grid, 256, 0, c.st>>>(n2, rhs, rhs_scale, W.jz, W.b);
+        k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, W.b, mkred(W, 0));
+        count_launch(2);
         double r2 = 0.0;
         PTROM_TRY(fetch(c, W.redout, &r2, 1));
         beta = sqrt(r2);
-        if (beta <= c.p->gmres_rtol * bnorm) break;
-        r0 = W.z;
+        if (beta <= c.p->gmres_rtol * bnorm) {
+            if (x_upd) {
+                k_axpy<<<c.grid, 256, 0, c.st>>>(n2, 1.0, d, x_upd);
+                count_launch();
+            }
+            break;
+        }
+        r0 = W.b;
+        r0_scale = 1.0;
+        r0_nrm2 = W.redout;
     }
-    // the last k_scale may have consumed W.z as r0; callers only read d.
     return PTROM_OK;
 }
 
@@ -588,6 +754,7 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
     c.grid = (c.n2 + 255) / 256;
     if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
     c.rgrid = red_grid(c.n2);
+    c.coop = cgs2_coop_fits(c.rgrid);
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;
     memset(c.stats, 0, sizeof(*c.stats));
@@ -622,9 +789,8 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
             k_blockdiag<<<c.grid, 256, 0, c.st>>>(n, W.D, W.r, c.hdt, -1.0, x, 1, 0);
             count_launch();
         } else if (p->jac_mode == PTROM_JAC_JFNK) {
-            PTROM_TRY(gmres(c, W.r, -1.0, W.d));
-            k_axpy<<<c.grid, 256, 0, c.st>>>(c.n2, 1.0, W.d, x);
-            count_launch();
+            // solve (I - hdt J) d = -r; x += d (slot 0 of redout holds ||r||^2)
+            PTROM_TRY(gmres(c, W.r, -1.0, W.d, x, W.redout, nr[0]));
         } else {
             if (refresh) PTROM_TRY(dense_factor(c));
             k_lu_solve<<<1, 1024, 0, c.st>>>(c.n2, W.M, W.perm, W.r, -1.0, W.d);
@@ -691,6 +857,7 @@ extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *
     c.grid = (c.n2 + 255) / 256;
     if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
     c.rgrid = red_grid(c.n2);
+    c.coop = cgs2_coop_fits(c.rgrid);
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;
     memset(c.stats, 0, sizeof(*c.stats));
@@ -700,7 +867,7 @@ extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *
     PTROM_TRY(velocity(n, x_n, n, x_n, Gamma, q.delta, W.fxi, W.D, q.prec, c.st, 0, W.pack));
     c.stats->velocity_evals++;
     // mu = (I - h J_n)^{-T} lambda
-    PTROM_TRY(gmres(c, lambda, 1.0, W.d));
+    PTROM_TRY(gmres(c, lambda, 1.0, W.d, nullptr));
     // gGamma += h F_n^T mu
     PTROM_TRY(vjp(n, x_n, Gamma, q.delta, W.d, nullptr, gtmp, q.prec, c.st, 0, W.pack));
     k_axpy<<<c.grid, 256, 0, c.st>>>(n, c.hdt, gtmp, gGamma);

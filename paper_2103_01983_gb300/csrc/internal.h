@@ -5,15 +5,23 @@
 
 namespace ptrom {
 
+// Optional epilogue of the J v / J^T w launches: with z != nullptr the
+// output is z - hdt * (J v) (the Newton matrix (I - hdt J) applied to z when
+// v = z), written in place of J v.
+struct LinEpi {
+    const double *z = nullptr;
+    double hdt = 0.0;
+};
+
 // All-pairs launches (bs_pair.cu).  split = 0 -> automatic cluster split.
 // scratch: device buffer of at least pack_scratch_bytes(ns) bytes for the
 // packed sources, or nullptr (stream-ordered allocation from the pool).
 int velocity(int nt, const double *xt, int ns, const double *xs, const double *G, double delta,
              double *f, double *D, int prec, cudaStream_t st, int split, void *scratch = nullptr);
 int jvp(int n, const double *x, const double *G, double delta, const double *v, double *jv,
-        int prec, cudaStream_t st, int split, void *scratch = nullptr);
+        int prec, cudaStream_t st, int split, void *scratch = nullptr, LinEpi lin = LinEpi{});
 int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
-        double *gG, int prec, cudaStream_t st, int split, void *scratch = nullptr);
+        double *gG, int prec, cudaStream_t st, int split, void *scratch = nullptr, LinEpi lin = LinEpi{});
 size_t pack_scratch_bytes(int ns);
 // Batched velocity (+ self blocks when D != nullptr) over B instances; S = source split.
 int velocity_batched(int B, const int *n, const double *const *x, const double *const *G, const double *delta,

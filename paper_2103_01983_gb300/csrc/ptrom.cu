@@ -412,6 +412,10 @@ static std::vector<float> to_f32_rows(const double *a, int rows, int cols, int l
 int ptrom::model_fill_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
                       const double *gamma_c) {
     DevModel &d = m->d;
+    if (x0_s) m->h_x0_s.assign(x0_s, x0_s + 2 * (size_t)d.ns);
+    if (phi_c) m->h_phi_c.assign(phi_c, phi_c + 2 * (size_t)d.Nc * d.M);
+    if (x0_c) m->h_x0_c.assign(x0_c, x0_c + 2 * (size_t)d.Nc);
+    if (gamma_c) m->h_gamma_c.assign(gamma_c, gamma_c + (size_t)d.Nc);
     if (x0_s) {
         std::vector<float> v(2 * (size_t)d.ns);
         for (int i = 0; i < d.ns; ++i) {
@@ -473,6 +477,11 @@ extern "C" int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **ou
     d.tol = s.tol;
     d.max_gn = s.max_gn;
     d.qr64 = s.qr_prec == PTROM_FP64;
+    m->qr_prec = s.qr_prec;
+    m->h_phi_s.assign(s.phi_s, s.phi_s + 2 * (size_t)s.n_s * s.M);
+    m->h_A.assign(s.A, s.A + (size_t)s.M_r * 2 * s.n_s);
+    m->h_off.assign(s.off, s.off + s.n_s + 1);
+    m->h_idx.assign(s.idx, s.idx + L);
     m->ox = s.x0_s[0];
     m->oy = s.x0_s[s.n_s];
     const SmemLayout lay = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64);

@@ -975,26 +975,28 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     m->A = Ah;
     m->cl_off = cl_off;
     m->cl_mem = cl_mem;
-    void *pd = nullptr;
-    int e = PTROM_OK;
-    if (cudaMalloc(&pd, sizeof(double) * Phi.size()) != cudaSuccess) e = PTROM_ENOMEM;
-    if (e == PTROM_OK) {
-        m->bufs.push_back(pd);
-        m->phi_dev = (double *)pd;
-        if (cudaMemcpy(pd, Phi.data(), sizeof(double) * Phi.size(), cudaMemcpyHostToDevice) != cudaSuccess) e = PTROM_ECUDA;
-    }
-    if (e == PTROM_OK && cudaMalloc(&pd, sizeof(double) * nd) != cudaSuccess) e = PTROM_ENOMEM;
-    if (e == PTROM_OK) {
-        m->bufs.push_back(pd);
-        m->x0_dev = (double *)pd;
-        if (cudaMemcpy(pd, x0h.data(), sizeof(double) * nd, cudaMemcpyHostToDevice) != cudaSuccess) e = PTROM_ECUDA;
-    }
+    const int e = model_store_basis(m, Phi.data(), x0h.data());
     if (e != PTROM_OK) {
         ptrom_free(m);
         return set_error(e, "ptrom_build: could not store the basis");
     }
     if (info) *info = inf;
     *out = m;
+    return PTROM_OK;
+}
+
+int ptrom::model_store_basis(ptrom_model *m, const double *phi, const double *x0) {
+    const size_t nphi = (size_t)2 * m->n * m->d.M, nd = 2 * (size_t)m->n;
+    void *pd = nullptr;
+    if (cudaMalloc(&pd, sizeof(double) * nphi) != cudaSuccess) return PTROM_ENOMEM;
+    m->bufs.push_back(pd);
+    m->phi_dev = (double *)pd;
+    if (cudaMemcpy(pd, phi, sizeof(double) * nphi, cudaMemcpyHostToDevice) != cudaSuccess) return PTROM_ECUDA;
+    if (cudaMalloc(&pd, sizeof(double) * nd) != cudaSuccess) return PTROM_ENOMEM;
+    m->bufs.push_back(pd);
+    m->x0_dev = (double *)pd;
+    if (cudaMemcpy(pd, x0, sizeof(double) * nd, cudaMemcpyHostToDevice) != cudaSuccess) return PTROM_ECUDA;
+    m->x0_full.assign(x0, x0 + nd);
     return PTROM_OK;
 }
 
@@ -1023,6 +1025,7 @@ extern "C" int ptrom_set_param_full(ptrom_model *m, const double *x0, const doub
     }
     PTROM_TRY(model_fill_param(m, x0_s.data(), phi_c.data(), x0_c.data(), g_c.data()));
     PTROM_CUDA(cudaMemcpyAsync(m->x0_dev, x0, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, st));
+    m->x0_full = xh;
     return PTROM_OK;
 }
 

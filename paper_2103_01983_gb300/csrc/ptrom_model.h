@@ -40,6 +40,10 @@ struct ptrom_model {
     double ox, oy;
     std::vector<void *> bufs;
     size_t smem;
+    // host FP64 copies of the description (kept for ptrom_save)
+    int qr_prec = 0;
+    std::vector<double> h_phi_s, h_x0_s, h_phi_c, h_x0_c, h_gamma_c, h_A;
+    std::vector<int> h_off, h_idx;
     // offline data, kept by models made with ptrom_build
     bool built = false;
     int n = 0;
@@ -49,6 +53,7 @@ struct ptrom_model {
     std::vector<double> A;        // [M_r][2 n_s] row-major
     std::vector<int> cl_off;      // [N_c + 1] cluster -> members (CSR)
     std::vector<int> cl_mem;
+    std::vector<double> x0_full;  // [2n] the current parameter's x^0 (host copy of x0_dev)
     double *phi_dev = nullptr;    // [2n][M] FP64 (reconstruction)
     double *x0_dev = nullptr;     // [2n]
 };
@@ -57,4 +62,7 @@ namespace ptrom {
 // Fill the parameter-dependent device arrays of a model from host arrays.
 int model_fill_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
                      const double *gamma_c);
+// Give a built model its FP64 basis and reference state on the device
+// (reconstruction); phi [2n][M] row-major, x0 [2n], host arrays.
+int model_store_basis(ptrom_model *m, const double *phi, const double *x0);
 }  // namespace ptrom

@@ -134,6 +134,8 @@ def _load():
         "bs_velocity_batched": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
         "fom_step_batched": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(FomStats), _vp], _i),
+        "ptrom_save": ([_vp, ctypes.c_char_p], _i),
+        "ptrom_load": ([ctypes.c_char_p, ctypes.POINTER(_vp)], _i),
         "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
         "fom_step": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                       ctypes.POINTER(FomStats), _vp], _i),
@@ -359,6 +361,17 @@ class PtromModel:
         _check(lib.ptrom_reconstruct(self.handle, _ptr(xhat), ctypes.c_void_p(rows.data_ptr()), rows.numel(),
                                      _ptr(out), _stream(stream)))
         return out
+
+    def save(self, path):
+        """Write the model to one binary file (ptrom_save)."""
+        _check(lib.ptrom_save(self.handle, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path):
+        """Create a model on the current device from a ptrom_save file."""
+        h = ctypes.c_void_p()
+        _check(lib.ptrom_load(os.fsencode(path), ctypes.byref(h)))
+        return cls._wrap(h)
 
     def new_state(self, device="cuda"):
         """Zero state: xhat = 0, carried velocity computed on the first step."""

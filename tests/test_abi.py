@@ -50,3 +50,23 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert L.bs_vjp(1, null, null, 0.1, null, null, null, 0, null) == -1
     assert L.ptrom_set_source_split(9) == -1
     assert L.ptrom_set_source_split(0) == 0
+
+
+def test_model_file_errors_before_any_cuda_call(lib, tmp_path):
+    """ptrom_load rejects missing, foreign, truncated and corrupted files on
+    the host (the hash and the header are checked before any upload)."""
+    L = lib.lib
+    h = ctypes.c_void_p(0)
+    assert L.ptrom_save(None, b"/nonexistent/x") == -1
+    assert L.ptrom_load(None, ctypes.byref(h)) == -1
+    assert L.ptrom_load(str(tmp_path / "missing.bin").encode(), ctypes.byref(h)) == -1
+    assert "cannot open" in lib.last_error()
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a model at all, just some bytes" * 4)
+    assert L.ptrom_load(str(junk).encode(), ctypes.byref(h)) == -1
+    assert "checksum" in lib.last_error()
+    assert not h.value
+    short = tmp_path / "short.bin"
+    short.write_bytes(b"PTROM")
+    assert L.ptrom_load(str(short).encode(), ctypes.byref(h)) == -1
+    assert "too short" in lib.last_error()

@@ -106,3 +106,67 @@ def test_set_param_full_is_identity_for_the_training_parameter(P):
     b = torch.zeros(10, dtype=torch.float64, device="cuda")
     P.ptrom_step([model], [s2], 20, xhat=[b])
     np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-6, atol=1e-12)
+
+
+def test_save_load_round_trip(P, tmp_path):
+    """A saved and reloaded model steps, reconstructs and reparametrises
+    exactly as the original (same arrays, same kernels)."""
+    x0, G = W.two_cluster(512, seed=0)
+    fp = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c")
+    model, _ = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 10, 20, 20, 30, fp, theta=0.5)
+    path = tmp_path / "model.ptrom"
+    model.save(path)
+    back = P.PtromModel.load(path)
+    assert (back.n, back.M, back.M_r, back.n_s, back.N_c) == (model.n, model.M, model.M_r, model.n_s, model.N_c)
+    qa, qb = model.query(), back.query()
+    for k in qa:
+        np.testing.assert_array_equal(qa[k], qb[k])
+
+    def run(m):
+        st = m.new_state()
+        xh = torch.zeros(10, dtype=torch.float64, device="cuda")
+        hist = torch.zeros(15, 10, dtype=torch.float64, device="cuda")
+        P.ptrom_step([m], [st], 15, xhat=[xh], hist=[hist])
+        return hist, m.reconstruct(xh)
+
+    ha, ra = run(model)
+    hb, rb = run(back)
+    assert torch.equal(ha, hb) and torch.equal(ra, rb)
+    # a new parameter, then a second save: the reparametrised arrays travel
+    x1, G1 = W.two_cluster(512, seed=0, sep=1.1, ratio=1.5)
+    model.set_param_full(_dev(x1), _dev(G1))
+    back.set_param_full(_dev(x1), _dev(G1))
+    path2 = tmp_path / "model2.ptrom"
+    back.save(path2)
+    back2 = P.PtromModel.load(path2)
+    ha, ra = run(model)
+    hb, rb = run(back2)
+    assert torch.equal(ha, hb) and torch.equal(ra, rb)
+    # a flipped byte anywhere is caught by the hash
+    raw = bytearray(path2.read_bytes())
+    raw[len(raw) // 2] ^= 0x10
+    bad = tmp_path / "bad.ptrom"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(RuntimeError, match="checksum"):
+        P.PtromModel.load(bad)
+
+
+def test_save_load_desc_model(P, tmp_path):
+    """A model created from arrays (not by ptrom_build) round-trips too."""
+    from _ptrom_cases import build_case, model_arrays
+    x0, G = W.disk(128, seed=1)
+    case = build_case(x0, G, 0.05, 0.01, 40, M=6, n_s=16, M_r=12, theta=0.5)
+    arr = model_arrays(case)
+    m = P.PtromModel(arr["phi_s"], arr["x0_s"], arr["phi_c"], arr["x0_c"], arr["gamma_c"], arr["A"],
+                     arr["off"], arr["idx"], case["dt"], case["delta"])
+    path = tmp_path / "desc.ptrom"
+    m.save(path)
+    back = P.PtromModel.load(path)
+
+    def run(mm):
+        st = mm.new_state()
+        xh = torch.zeros(mm.M, dtype=torch.float64, device="cuda")
+        P.ptrom_step([mm], [st], 10, xhat=[xh])
+        return xh
+
+    assert torch.equal(run(m), run(back))
