@@ -233,7 +233,10 @@ def run_ours(args):
     clk.start()
     time.sleep(0.25)
     ptrom.timing_read()
-    ptrom.timing_enable(True)
+    # the timed region brackets only the all-pairs launches with events (the
+    # small kernels' events would add gaps of their own); the step breakdown
+    # below comes from a separate instrumented pass
+    ptrom.timing_enable(True, kinds=list(FLOPS_PER_PAIR))
     l0 = ptrom.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -271,7 +274,7 @@ def run_ours(args):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_count, sm_mhz)
-    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom = max((k for k in ktimes if k in FLOPS_PER_PAIR), key=lambda k: ktimes[k][0])
     dom_ms, dom_cnt = ktimes[dom]
     achieved = FLOPS_PER_PAIR[dom] * n * n * dom_cnt / (dom_ms * 1e-3) / 1e12 if dom_cnt else None
     traffic = _traffic(dom, n)
@@ -283,7 +286,8 @@ def run_ours(args):
     kernels = {k: {"launches": c, "avg_us": 1e3 * t / c,
                    "pairs_per_s": n * n * c / (t * 1e-3),
                    "tflops": FLOPS_PER_PAIR[k] * n * n * c / (t * 1e-3) / 1e12}
-               for k, (t, c) in ktimes.items() if c}
+               for k, (t, c) in ktimes.items() if c and k in FLOPS_PER_PAIR}
+    other = _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush)
 
     # end to end: host buffers, H2D of the step's inputs and D2H of its result
     e2e = _e2e(args, ptrom, params, x0, G, dev, stream, n)
@@ -296,6 +300,7 @@ def run_ours(args):
         "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         "step_stats": {k: v / args.steps for k, v in agg.items()},
         "kernels": kernels,
+        "step_breakdown": other,
     }
     if rank == 0 and not args.no_ptrom:
         line["ptrom"] = ptrom_leg(ptrom, dev, ms_all / args.steps)
@@ -461,6 +466,31 @@ def batch_leg(ptrom, dev):
         "batched_fom_step_pairs_per_s": evals_b / tb_step,
         "fom_mode": "block-diagonal inexact Newton (the paper's), FP32C pair sums",
     }
+
+
+def _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush, steps=10):
+    """Untimed-region diagnostic: every library launch kind event-timed over a
+    few steps -> per-step device time of each kind and the rest of the step
+    (launch gaps, copies, host waits).  These events add gaps of their own, so
+    the step here is longer than in the timed region."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ptrom.timing_read()
+    ptrom.timing_enable(True)
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ptrom.fom_step(params, Gt, x, f, work=work)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ptrom.timing_enable(False)
+    kt = ptrom.timing_read()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    out = {k: {"launches_per_step": c / steps, "us_per_step": 1e3 * t / steps}
+           for k, (t, c) in kt.items() if c}
+    out["rest_us_per_step"] = 1e3 * (ms - sum(t for t, _ in kt.values())) / steps
+    out["step_us_instrumented"] = 1e3 * ms / steps
+    return out
 
 
 def _traffic(kind, n):

@@ -63,9 +63,13 @@ int ptrom_set_source_split(int S);
 
 /* Instrumentation (host-side, process-wide).
  * ptrom_launch_count: number of CUDA kernels the library has launched so far.
- * ptrom_timing_enable(1): from now on every all-pairs launch is bracketed by
- *   two CUDA events recorded on the launch's own stream (up to 65536 launches;
- *   later ones are not timed); ptrom_timing_enable(0) stops recording.
+ * ptrom_timing_enable(on): on = 0 stops recording; on = 1 brackets every
+ *   timed launch of any kind below with two CUDA events recorded on the
+ *   launch's own stream (up to 65536 launches; later ones are not timed);
+ *   any other positive `on` is a bit mask (bit k = kind k) of the kinds to
+ *   time, so a caller can time the all-pairs kernels alone (the events of
+ *   the small kinds add launch gaps of their own); bit 30 is ignored, so
+ *   (1 << 30) | 1 times kind 0 alone.
  * ptrom_timing_read: synchronises the recorded events and returns, for each
  *   kernel kind k < nkinds (enum ptrom_kernel_kind), the summed device time in
  *   milliseconds (ms[k]) and the number of timed launches (count[k]); then
@@ -77,7 +81,11 @@ enum ptrom_kernel_kind {
     PTROM_K_VJP = 3,
     PTROM_K_JPHI = 4,
     PTROM_K_PTROM_STEP = 5,
-    PTROM_K_NKINDS = 6
+    PTROM_K_PACK = 6,          /* source packing before an all-pairs launch     */
+    PTROM_K_FOM_VEC = 7,       /* FOM vector kernels: residual, normalise +
+                                  precondition, GMRES correction, updates      */
+    PTROM_K_FOM_ORTH = 8,      /* FOM CGS2 orthogonalisation + least squares    */
+    PTROM_K_NKINDS = 9
 };
 long long ptrom_launch_count(void);
 int ptrom_timing_enable(int on);

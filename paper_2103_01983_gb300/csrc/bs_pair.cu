@@ -16,6 +16,21 @@
 #include "internal.h"
 #include "pairsum.cuh"
 
+// Resident CTAs per SM each op's register budget must allow (compile-time
+// tunables; the defaults are the measured best on GB300).
+#ifndef PTROM_MINB_VEL
+#define PTROM_MINB_VEL 4
+#endif
+#ifndef PTROM_MINB_VELD
+#define PTROM_MINB_VELD 2
+#endif
+#ifndef PTROM_MINB_JVP
+#define PTROM_MINB_JVP 3
+#endif
+#ifndef PTROM_MINB_VJP
+#define PTROM_MINB_VJP 3
+#endif
+
 namespace ptrom {
 
 struct Origin2 {
@@ -43,7 +58,7 @@ struct VelOp {
     using V = typename T2::V;
     using Origin = Origin2;
     static constexpr int NACC = WITH_D ? 5 : 2;
-    static constexpr int kMinBlocks = (WITH_D || sizeof(R) == 8) ? 2 : 4;
+    static constexpr int kMinBlocks = sizeof(R) == 8 ? 2 : (WITH_D ? PTROM_MINB_VELD : PTROM_MINB_VEL);
     static constexpr int kKind = WITH_D ? PTROM_K_VELOCITY_D : PTROM_K_VELOCITY;
     struct Args {
         int nt, ns;
@@ -120,7 +135,7 @@ struct JvpOp {
     using V = typename T2::V;
     using Origin = Origin2;
     static constexpr int NACC = 4;
-    static constexpr int kMinBlocks = sizeof(R) == 8 ? 2 : 3;
+    static constexpr int kMinBlocks = sizeof(R) == 8 ? 2 : PTROM_MINB_JVP;
     static constexpr int kKind = PTROM_K_JVP;
     struct Args {
         int n;
@@ -200,7 +215,7 @@ struct VjpOp {
     using V = typename T2::V;
     using Origin = Origin2;
     static constexpr int NACC = (GX ? 4 : 0) + (GG ? 1 : 0);
-    static constexpr int kMinBlocks = sizeof(R) == 8 ? 2 : 3;
+    static constexpr int kMinBlocks = sizeof(R) == 8 ? 2 : PTROM_MINB_VJP;
     static constexpr int kKind = PTROM_K_VJP;
     struct Args {
         int n;
@@ -287,50 +302,50 @@ struct VjpOp {
 // ---------------------------------------------------------------- dispatch
 template <typename R>
 static int velocity_impl(int nt, const double *xt, int ns, const double *xs, const double *G,
-                         double delta, double *f, double *D, cudaStream_t st, int split, void *scr) {
+                         double delta, double *f, double *D, cudaStream_t st, const LaunchOpts &o) {
     if (D) {
         typename VelOp<R, true, true>::Args a{nt, ns, xt, xs, G, delta, f, D};
-        return launch_pairs<VelOp<R, true, true>>(a, nt, ns, st, split, scr);
+        return launch_pairs<VelOp<R, true, true>>(a, nt, ns, st, o);
     }
     if (delta == 0.0) {
         typename VelOp<R, false, true>::Args a{nt, ns, xt, xs, G, delta, f, nullptr};
-        return launch_pairs<VelOp<R, false, true>>(a, nt, ns, st, split, scr);
+        return launch_pairs<VelOp<R, false, true>>(a, nt, ns, st, o);
     }
     typename VelOp<R, false, false>::Args a{nt, ns, xt, xs, G, delta, f, nullptr};
-    return launch_pairs<VelOp<R, false, false>>(a, nt, ns, st, split, scr);
+    return launch_pairs<VelOp<R, false, false>>(a, nt, ns, st, o);
 }
 
 template <typename R>
 static int jvp_impl(int n, const double *x, const double *G, double delta, const double *v,
-                    double *jv, cudaStream_t st, int split, void *scr, LinEpi lin) {
+                    double *jv, cudaStream_t st, const LaunchOpts &o) {
     if (delta == 0.0) {
-        typename JvpOp<R, true>::Args a{n, x, G, v, delta, jv, lin.z, lin.hdt};
-        return launch_pairs<JvpOp<R, true>>(a, n, n, st, split, scr);
+        typename JvpOp<R, true>::Args a{n, x, G, v, delta, jv, o.lin.z, o.lin.hdt};
+        return launch_pairs<JvpOp<R, true>>(a, n, n, st, o);
     }
-    typename JvpOp<R, false>::Args a{n, x, G, v, delta, jv, lin.z, lin.hdt};
-    return launch_pairs<JvpOp<R, false>>(a, n, n, st, split, scr);
+    typename JvpOp<R, false>::Args a{n, x, G, v, delta, jv, o.lin.z, o.lin.hdt};
+    return launch_pairs<JvpOp<R, false>>(a, n, n, st, o);
 }
 
 template <typename R, bool MASK>
 static int vjp_impl2(int n, const double *x, const double *G, double delta, const double *w,
-                     double *gx, double *gG, cudaStream_t st, int split, void *scr, LinEpi lin) {
+                     double *gx, double *gG, cudaStream_t st, const LaunchOpts &o) {
     if (gx && gG) {
-        typename VjpOp<R, MASK, true, true>::Args a{n, x, G, w, delta, gx, gG, lin.z, lin.hdt};
-        return launch_pairs<VjpOp<R, MASK, true, true>>(a, n, n, st, split, scr);
+        typename VjpOp<R, MASK, true, true>::Args a{n, x, G, w, delta, gx, gG, o.lin.z, o.lin.hdt};
+        return launch_pairs<VjpOp<R, MASK, true, true>>(a, n, n, st, o);
     }
     if (gx) {
-        typename VjpOp<R, MASK, true, false>::Args a{n, x, G, w, delta, gx, gG, lin.z, lin.hdt};
-        return launch_pairs<VjpOp<R, MASK, true, false>>(a, n, n, st, split, scr);
+        typename VjpOp<R, MASK, true, false>::Args a{n, x, G, w, delta, gx, gG, o.lin.z, o.lin.hdt};
+        return launch_pairs<VjpOp<R, MASK, true, false>>(a, n, n, st, o);
     }
     typename VjpOp<R, MASK, false, true>::Args a{n, x, G, w, delta, gx, gG, nullptr, 0.0};
-    return launch_pairs<VjpOp<R, MASK, false, true>>(a, n, n, st, split, scr);
+    return launch_pairs<VjpOp<R, MASK, false, true>>(a, n, n, st, o);
 }
 
 template <typename R>
 static int vjp_impl(int n, const double *x, const double *G, double delta, const double *w,
-                    double *gx, double *gG, cudaStream_t st, int split, void *scr, LinEpi lin) {
-    if (delta == 0.0) return vjp_impl2<R, true>(n, x, G, delta, w, gx, gG, st, split, scr, lin);
-    return vjp_impl2<R, false>(n, x, G, delta, w, gx, gG, st, split, scr, lin);
+                    double *gx, double *gG, cudaStream_t st, const LaunchOpts &o) {
+    if (delta == 0.0) return vjp_impl2<R, true>(n, x, G, delta, w, gx, gG, st, o);
+    return vjp_impl2<R, false>(n, x, G, delta, w, gx, gG, st, o);
 }
 
 static int check_common(const char *fn, int nt, int ns, double delta, int prec) {
@@ -342,19 +357,19 @@ static int check_common(const char *fn, int nt, int ns, double delta, int prec) 
 
 // Internal entry points used by the solvers (explicit source split for tests).
 int velocity(int nt, const double *xt, int ns, const double *xs, const double *G, double delta,
-             double *f, double *D, int prec, cudaStream_t st, int split, void *scr) {
-    return prec == PTROM_FP64 ? velocity_impl<double>(nt, xt, ns, xs, G, delta, f, D, st, split, scr)
-                              : velocity_impl<float>(nt, xt, ns, xs, G, delta, f, D, st, split, scr);
+             double *f, double *D, int prec, cudaStream_t st, const LaunchOpts &o) {
+    return prec == PTROM_FP64 ? velocity_impl<double>(nt, xt, ns, xs, G, delta, f, D, st, o)
+                              : velocity_impl<float>(nt, xt, ns, xs, G, delta, f, D, st, o);
 }
 int jvp(int n, const double *x, const double *G, double delta, const double *v, double *jv,
-        int prec, cudaStream_t st, int split, void *scr, LinEpi lin) {
-    return prec == PTROM_FP64 ? jvp_impl<double>(n, x, G, delta, v, jv, st, split, scr, lin)
-                              : jvp_impl<float>(n, x, G, delta, v, jv, st, split, scr, lin);
+        int prec, cudaStream_t st, const LaunchOpts &o) {
+    return prec == PTROM_FP64 ? jvp_impl<double>(n, x, G, delta, v, jv, st, o)
+                              : jvp_impl<float>(n, x, G, delta, v, jv, st, o);
 }
 int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
-        double *gG, int prec, cudaStream_t st, int split, void *scr, LinEpi lin) {
-    return prec == PTROM_FP64 ? vjp_impl<double>(n, x, G, delta, w, gx, gG, st, split, scr, lin)
-                              : vjp_impl<float>(n, x, G, delta, w, gx, gG, st, split, scr, lin);
+        double *gG, int prec, cudaStream_t st, const LaunchOpts &o) {
+    return prec == PTROM_FP64 ? vjp_impl<double>(n, x, G, delta, w, gx, gG, st, o)
+                              : vjp_impl<float>(n, x, G, delta, w, gx, gG, st, o);
 }
 size_t pack_scratch_bytes(int ns) { return pack_scratch_bytes_impl(ns); }
 
@@ -406,7 +421,7 @@ extern "C" int bs_velocity(int nt, const double *xt, int ns, const double *xs, c
                            ptrom_stream_t stream) {
     PTROM_TRY(check_common("bs_velocity", nt, ns, delta, prec));
     if (!xt || !xs || !Gamma || !f_out) return set_error(PTROM_EINVAL, "bs_velocity: NULL array");
-    return velocity(nt, xt, ns, xs, Gamma, delta, f_out, selfjac_out, prec, (cudaStream_t)stream, 0);
+    return velocity(nt, xt, ns, xs, Gamma, delta, f_out, selfjac_out, prec, (cudaStream_t)stream);
 }
 
 extern "C" int bs_jvp(int n, const double *x, const double *Gamma, double delta, const double *v,
@@ -414,7 +429,7 @@ extern "C" int bs_jvp(int n, const double *x, const double *Gamma, double delta,
     PTROM_TRY(check_common("bs_jvp", n, n, delta, prec));
     if (n < 2) return set_error(PTROM_EINVAL, "bs_jvp: n must be >= 2");
     if (!x || !Gamma || !v || !jv) return set_error(PTROM_EINVAL, "bs_jvp: NULL array");
-    return jvp(n, x, Gamma, delta, v, jv, prec, (cudaStream_t)stream, 0);
+    return jvp(n, x, Gamma, delta, v, jv, prec, (cudaStream_t)stream);
 }
 
 extern "C" int bs_vjp(int n, const double *x, const double *Gamma, double delta, const double *w,
@@ -423,5 +438,5 @@ extern "C" int bs_vjp(int n, const double *x, const double *Gamma, double delta,
     if (n < 2) return set_error(PTROM_EINVAL, "bs_vjp: n must be >= 2");
     if (!x || !Gamma || !w) return set_error(PTROM_EINVAL, "bs_vjp: NULL array");
     if (!gx_out && !gGamma_out) return PTROM_OK;
-    return vjp(n, x, Gamma, delta, w, gx_out, gGamma_out, prec, (cudaStream_t)stream, 0);
+    return vjp(n, x, Gamma, delta, w, gx_out, gGamma_out, prec, (cudaStream_t)stream);
 }

@@ -38,6 +38,11 @@ int scratch_trim();  // release the current device pool's cached blocks
 // CUDA-event timing of one launch (no-op unless ptrom_timing_enable(1)).
 int timing_begin(int kind, cudaStream_t st);
 void timing_end(int slot, cudaStream_t st);
+void timing_discard(int slot);  // leave a launch out of the totals (it did no work)
+// Per-thread, per-device pinned host buffer of at least `ndoubles` doubles and
+// `nevents` events (timing disabled): small device-to-host status reads that
+// the host waits for on an event while later work stays queued.
+int host_mailbox(size_t ndoubles, int nevents, double **host, cudaEvent_t **events);
 
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;  // 1 / (2 pi)
 

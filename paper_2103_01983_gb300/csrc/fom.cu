@@ -65,13 +65,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 // After every block has written its nk partials: the last block sums them
 // into red.out (warp w takes k = w, w + nwarps, ...; lanes stride the blocks;
 // fixed order, so the result is deterministic) and resets the counter.
-__device__ __forceinline__ void finish_reduction(const Red &red, int nk) {
+// Returns true in the last block, after a barrier (red.out readable by all
+// of its threads).
+__device__ __forceinline__ bool finish_reduction(const Red &red, int nk) {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(red.counter, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!last) return;
+    if (!last) return false;
     __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = warp; k < nk; k += nw) {
@@ -81,11 +83,18 @@ __device__ __forceinline__ void finish_reduction(const Red &red, int nk) {
         if (lane == 0) red.out[k] = s;
     }
     if (threadIdx.x == 0) *red.counter = 0u;
+    __syncthreads();
+    return true;
 }
 
-// r = xi - xprev - hdt (fxi + fprev);   out = {||r||^2, ||xi||^2}
+// r = xi - xprev - hdt (fxi + fprev);   out = {||r||^2, ||xi||^2}.
+// The last block also takes the Newton decision (converged when
+// ||r|| <= tol max(1, ||xi||)): st = {stop, ||r||, ||xi||} with stop 0 = go on,
+// 1 = converged, 2 = non-finite residual, 3 = iteration limit (limit set);
+// flags[0] = (stop != 0) lets queued Newton-update kernels skip themselves.
 __global__ void k_residual(int n2, const double *xi, const double *xprev, const double *fxi,
-                           const double *fprev, double hdt, double *r, Red red) {
+                           const double *fprev, double hdt, double *r, Red red, double tol, int limit, int *flags,
+                           double *st) {
     __shared__ double sh[32];
     double s0 = 0.0, s1 = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
@@ -100,7 +109,15 @@ __global__ void k_residual(int n2, const double *xi, const double *xprev, const 
         red.partials[blockIdx.x * 2 + 0] = t0;
         red.partials[blockIdx.x * 2 + 1] = t1;
     }
-    finish_reduction(red, 2);
+    if (finish_reduction(red, 2) && threadIdx.x == 0) {
+        const double rn = sqrt(red.out[0]), xn = sqrt(red.out[1]);
+        const bool conv = rn <= tol * (xn > 1.0 ? xn : 1.0);
+        const int stop = !isfinite(rn) ? 2 : (conv ? 1 : (limit ? 3 : 0));
+        flags[0] = stop != 0;
+        st[0] = stop;
+        st[1] = rn;
+        st[2] = xn;
+    }
 }
 
 // out[k] = <V_k, w> for k < K (V: K rows of length n2); with V == nullptr,
@@ -108,7 +125,8 @@ __global__ void k_residual(int n2, const double *xi, const double *xprev, const 
 // (at most kMaxPer per thread), warps reduce every dot by shuffles, one CTA
 // barrier combines the warps.
 constexpr int kMaxPer = 8;
-__global__ void k_multidot(int n2, int K, const double *V, const double *w, Red red) {
+__global__ void k_multidot(int n2, int K, const double *V, const double *w, Red red, const int *skip = nullptr) {
+    if (skip && *skip) return;
     __shared__ double sh[kRedThreads / 32][kMaxDots];
     const int stride = gridDim.x * blockDim.x;
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,7 +158,9 @@ __global__ void k_multidot(int n2, int K, const double *V, const double *w, Red 
 }
 
 // w -= sum_k h[k] V_k;  out[0] = ||w||^2
-__global__ void k_orth_update(int n2, int K, const double *V, const double *h, double *w, Red red) {
+__global__ void k_orth_update(int n2, int K, const double *V, const double *h, double *w, Red red,
+                              const int *skip = nullptr) {
+    if (skip && *skip) return;
     __shared__ double sh[32];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
@@ -187,7 +207,8 @@ __global__ void k_blockdiag(int n, const double *D, const double *v, double hdt,
 //   v = scale * src / (|scale| sqrt(*nrm2))  -> V_out,   z = M^{-1} v
 // (*nrm2 = ||src||^2 on the device, so the host need not read it first).
 __global__ void k_norm_precond(int n, const double *src, double scale, const double *nrm2, const double *D,
-                               double hdt, int transpose, double *V_out, double *z) {
+                               double hdt, int transpose, double *V_out, double *z, const int *skip) {
+    if (*skip) return;
     const double inv = 1.0 / (fabs(scale) * sqrt(*nrm2));
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double v0 = inv * (scale * src[i]), v1 = inv * (scale * src[n + i]);
@@ -200,19 +221,87 @@ __global__ void k_norm_precond(int n, const double *src, double scale, const dou
     }
 }
 
-// GMRES correction of one cycle: d += M^{-1} (sum_k y_k V_k); with x given,
-// also x += d (the Newton update after the last cycle).
-struct Coef {
-    double y[kMaxRestart];
+// GMRES least-squares state of one cycle on the device: the rotated
+// Hessenberg matrix H [(m+1) x m] (row-major, leading dimension m), the Givens
+// cosines and sines, the rotated right-hand side g [m+1], and
+// scal = {||b|| (first cycle), this cycle's initial residual norm}.
+struct GmDev {
+    double *H, *cs, *sn, *g, *scal;
 };
-__global__ void k_combine_precond(int n, int K, const double *V, Coef c, const double *D, double hdt, int transpose,
-                                  double *d, double *x) {
+
+// One Arnoldi column into the least squares (the host-side Givens update of
+// GMRES moved to the device): column j of H from the two CGS passes (h1 + h2)
+// and ||w|| (nrm2 = ||w||^2), the previous rotations applied, a new one
+// chosen, g rotated.  beta2: device address of the cycle's initial squared
+// norm (scaled by beta_scale^2).  Writes st = {stop, ||w||, |g_{j+1}|,
+// ||b||} with stop 0 = go on, 1 = converged (|g_{j+1}| <= rtol ||b||), at the
+// iteration limit or breakdown (||w|| = 0), 2 = non-finite; flags[0] = stop != 0.
+__device__ void givens_column(GmDev gm, int m, int j, const double *h1, const double *h2, double nrm2,
+                              const double *beta2, double beta_scale, int first_cycle, double rtol, int total,
+                              int max_iter, int *flags, double *st) {
+    double *H = gm.H;
+    if (j == 0) {
+        const double beta = fabs(beta_scale) * sqrt(*beta2);
+        gm.g[0] = beta;
+        gm.scal[1] = beta;
+        if (first_cycle) gm.scal[0] = beta;
+    }
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+    const double hn = sqrt(nrm2);
+    H[(size_t)(j + 1) * m + j] = hn;
+    int stop = 0;
+    if (!isfinite(hn)) {
+        stop = 2;
+    } else {
+        for (int i = 0; i < j; ++i) {
+            const double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
+            H[(size_t)i * m + j] = gm.cs[i] * a + gm.sn[i] * b2;
+            H[(size_t)(i + 1) * m + j] = -gm.sn[i] * a + gm.cs[i] * b2;
+        }
+        const double a = H[(size_t)j * m + j], b2 = H[(size_t)(j + 1) * m + j];
+        const double rr = hypot(a, b2);
+        gm.cs[j] = rr > 0 ? a / rr : 1.0;
+        gm.sn[j] = rr > 0 ? b2 / rr : 0.0;
+        H[(size_t)j * m + j] = rr;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        gm.g[j + 1] = -gm.sn[j] * gm.g[j];
+        gm.g[j] = gm.cs[j] * gm.g[j];
+        if (fabs(gm.g[j + 1]) <= rtol * gm.scal[0] || total >= max_iter || hn == 0.0) stop = 1;
+    }
+    flags[0] = stop != 0;
+    st[0] = stop;
+    st[1] = hn;
+    st[2] = fabs(gm.g[j + 1]);
+    st[3] = gm.scal[0];
+}
+
+// GMRES correction of one cycle of K steps: y = R^{-1} g (R = the leading
+// K x K block of the rotated H; each block solves it, warp 0, in shared
+// memory), then d += M^{-1} (sum_k y_k V_k); with x given, also x += d (the
+// Newton update after the last cycle).
+__global__ void k_combine_precond(int n, int K, int m, const double *V, GmDev gm, const double *D, double hdt,
+                                  int transpose, double *d, double *x) {
+    __shared__ double y[kMaxRestart];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int i = K - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1 + lane; k < K; k += 32) s += gm.H[(size_t)i * m + k] * y[k];
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double hii = gm.H[(size_t)i * m + i];
+                y[i] = hii != 0.0 ? (gm.g[i] - s) / hii : 0.0;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
     const size_t n2 = 2 * (size_t)n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double u0 = 0.0, u1 = 0.0;
         for (int k = 0; k < K; ++k) {
-            u0 += c.y[k] * V[k * n2 + i];
-            u1 += c.y[k] * V[k * n2 + n + i];
+            u0 += y[k] * V[k * n2 + i];
+            u1 += y[k] * V[k * n2 + n + i];
         }
         double z0, z1;
         bd_solve(D, n, i, hdt, transpose, u0, u1, 1.0, z0, z1);
@@ -238,10 +327,23 @@ __global__ void k_restart_res(int n2, const double *rhs, double scale, const dou
 // barrier -> every block sums the partials in the same fixed order (so all
 // blocks hold identical coefficients) -> w -= sum_k h_k V_k.  Outputs:
 // out[0..K) = first-pass h, out[kMaxDots..) = second-pass h,
-// out[2 kMaxDots] = ||w||^2 after both passes; w is written back.
+// out[2 kMaxDots] = ||w||^2 after both passes; w is written back.  Block 0
+// then adds the column to the least squares (givens_column, arguments G).
 // partials: 2 * gridDim.x * kMaxDots + gridDim.x doubles.
+struct GivensArgs {
+    GmDev gm;
+    int m;
+    const double *beta2;
+    double beta_scale;
+    int first_cycle;
+    double rtol;
+    int total, max_iter;
+    int *flags;
+    double *st;
+};
 __global__ void __launch_bounds__(kRedThreads)
-k_cgs2(int n2, int K, const double *V, double *w, double *partials, double *out) {
+k_cgs2(int n2, int K, const double *V, double *w, double *partials, double *out, GivensArgs ga, const int *skip) {
+    if (*skip) return;  // uniform over the grid: no block reaches a grid barrier
     cg::grid_group grid = cg::this_grid();
     __shared__ double sh[kRedThreads / 32][kMaxDots];
     __shared__ double hs[kMaxDots];
@@ -318,8 +420,20 @@ k_cgs2(int n2, int K, const double *V, double *w, double *partials, double *out)
         double t = 0.0;
         for (int b = lane; b < G; b += 32) t += Pn[b];
         t = warp_sum(t);
-        if (lane == 0) out[2 * kMaxDots] = t;
+        if (lane == 0) {
+            out[2 * kMaxDots] = t;
+            givens_column(ga.gm, ga.m, K - 1, out, out + kMaxDots, t, ga.beta2, ga.beta_scale, ga.first_cycle,
+                          ga.rtol, ga.total, ga.max_iter, ga.flags, ga.st);
+        }
     }
+}
+
+// The same least-squares update after the four-launch CGS2 (grids too large
+// to be co-resident): one thread.
+__global__ void k_givens(int K, const double *out, GivensArgs ga, const int *skip) {
+    if (*skip) return;
+    givens_column(ga.gm, ga.m, K - 1, out, out + kMaxDots, out[2 * kMaxDots], ga.beta2, ga.beta_scale,
+                  ga.first_cycle, ga.rtol, ga.total, ga.max_iter, ga.flags, ga.st);
 }
 
 // y += a * x
@@ -440,10 +554,18 @@ __global__ void k_lu_solve(int m, const double *A, const int *perm, const double
 }
 
 // ---------------------------------------------------------------- workspace
+// Status records copied to the host: slot 0 the Newton residual
+// {stop, ||r||, ||x||}, slot 1 + j Arnoldi step j {stop, ||w||, |g_{j+1}|, ||b||}.
+constexpr int kStatDoubles = 4;
+constexpr int kStatSlots = kMaxRestart + 1;
+
 struct Work {
     double *xprev, *fprev, *fxi, *r, *D, *d, *jz, *w, *z, *b, *V, *partials, *redout, *M;
+    double *stat;  // [kStatSlots][kStatDoubles]
+    GmDev gm;
     void *pack;
     unsigned int *counter;
+    int *flags;    // flags[0]: skip the queued Newton-update kernels
     int *perm, *status;
     size_t bytes;
 };
@@ -485,6 +607,13 @@ static Work layout(const ptrom_fom_params *p, int n, char *base) {
     W.partials = (double *)take(((size_t)2 * rg * kMaxDots + rg) * 8);
     W.redout = (double *)take(4 * kMaxDots * 8);
     W.counter = (unsigned int *)take(64);
+    W.flags = (int *)take(64);
+    W.stat = (double *)take(sizeof(double) * kStatSlots * kStatDoubles);
+    W.gm.H = (double *)take(sizeof(double) * (kMaxRestart + 1) * kMaxRestart);
+    W.gm.cs = (double *)take(sizeof(double) * kMaxRestart);
+    W.gm.sn = (double *)take(sizeof(double) * kMaxRestart);
+    W.gm.g = (double *)take(sizeof(double) * (kMaxRestart + 1));
+    W.gm.scal = (double *)take(sizeof(double) * 2);
     W.pack = take(pack_scratch_bytes(n));
     if (p->jac_mode == PTROM_JAC_DENSE) {
         W.M = (double *)take(n2 * n2 * 8);
@@ -530,6 +659,8 @@ struct Ctx {
     int grid, rgrid;
     bool coop = false;  // CGS2 as one cooperative kernel (rgrid blocks co-resident)
     ptrom_fom_stats *stats;
+    double *mb = nullptr;        // pinned status mailbox [kStatSlots][kStatDoubles]
+    cudaEvent_t *ev = nullptr;   // one event per mailbox slot
 };
 
 // Whether `blocks` CTAs of k_cgs2 fit on the device at once.
@@ -545,151 +676,181 @@ static bool cgs2_coop_fits(int blocks) {
 
 static Red mkred(const Work &W, int slot) { return Red{W.partials, W.counter, W.redout + slot * kMaxDots}; }
 
+// A launch timed under `kind` (ptrom_timing_*); its slot goes to *slots when given.
+#define PTROM_TIMED(kind, stream, slots, ...)             \
+    do {                                                  \
+        const int _slot = timing_begin((kind), (stream)); \
+        __VA_ARGS__;                                      \
+        timing_end(_slot, (stream));                      \
+        if (slots) (slots)->add(_slot);                   \
+    } while (0)
+static void discard(Slots &s) {
+    for (int i = 0; i < s.n; ++i) timing_discard(s.s[i]);
+    s.n = 0;
+}
+
 static int fetch(const Ctx &c, const double *dev, double *host, int count) {
     PTROM_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, c.st));
     PTROM_CUDA(cudaStreamSynchronize(c.st));
     return PTROM_OK;
 }
 
-// out = J v, or with lin set out = (I - hdt J) v, through the all-pairs
-// J v kernel (J^T w for the adjoint solves).
-static int apply_jvp(Ctx &c, const double *v, double *out, bool lin) {
-    LinEpi L;
-    if (lin) {
-        L.z = v;
-        L.hdt = c.hdt;
-    }
-    if (c.transpose) {
-        PTROM_TRY(vjp(c.n, c.xi, c.G, c.p->delta, v, out, nullptr, c.p->prec, c.st, 0, c.W.pack, L));
-    } else {
-        PTROM_TRY(jvp(c.n, c.xi, c.G, c.p->delta, v, out, c.p->prec, c.st, 0, c.W.pack, L));
-    }
-    if (c.stats) c.stats->jvp_evals++;
+// Queue the copy of status slot k to the pinned mailbox and its event.
+static int post(Ctx &c, int k) {
+    PTROM_CUDA(cudaMemcpyAsync(c.mb + k * kStatDoubles, c.W.stat + k * kStatDoubles, sizeof(double) * kStatDoubles,
+                               cudaMemcpyDeviceToHost, c.st));
+    PTROM_CUDA(cudaEventRecord(c.ev[k], c.st));
     return PTROM_OK;
 }
 
-// CGS2 of W.w against V_0..V_{K-1}: first-pass h at redout slot 1, second-pass
-// h at slot 2, ||w||^2 at slot 3 (one cooperative launch, or four launches
-// when the grid cannot be co-resident).
-static int cgs2(Ctx &c, int K) {
+// Wait for status slot k (the stream may hold later work) and return it.
+static const double *wait_post(Ctx &c, int k) {
+    if (cudaEventSynchronize(c.ev[k]) != cudaSuccess) return nullptr;
+    return c.mb + k * kStatDoubles;
+}
+
+// out = J v, or with lin set out = (I - hdt J) v, through the all-pairs
+// J v kernel (J^T w for the adjoint solves).
+static int apply_jvp(Ctx &c, const double *v, double *out, bool lin, const int *skip = nullptr,
+                     Slots *slots = nullptr) {
+    LaunchOpts o;
+    o.scratch = c.W.pack;
+    o.skip = skip;
+    o.slots = slots;
+    if (lin) {
+        o.lin.z = v;
+        o.lin.hdt = c.hdt;
+    }
+    if (c.transpose) {
+        PTROM_TRY(vjp(c.n, c.xi, c.G, c.p->delta, v, out, nullptr, c.p->prec, c.st, o));
+    } else {
+        PTROM_TRY(jvp(c.n, c.xi, c.G, c.p->delta, v, out, c.p->prec, c.st, o));
+    }
+    return PTROM_OK;
+}
+
+// One GMRES cycle's fixed launch arguments.
+struct Cycle {
+    const double *r0;       // cycle start vector (times r0_scale)
+    double r0_scale;
+    const double *r0_nrm2;  // device ||r0||^2
+    int first;              // first cycle (defines ||b||)
+    int total;              // Arnoldi steps taken in earlier cycles
+};
+
+// Queue Arnoldi step j of a cycle; every kernel of it skips itself when
+// flags[0] is set (an earlier step or the Newton test already stopped), so a
+// step may be queued before the previous one's outcome is known.
+static int queue_step(Ctx &c, const Cycle &cy, int j, Slots *slots) {
     Work &W = c.W;
-    int n2 = c.n2;
+    const int n2 = c.n2, m = c.p->gmres_restart;
+    const int *skip = W.flags;
+    double *vj = W.V + (size_t)j * n2;
+    // v_j = previous Krylov vector / its norm (read on the device); z = M^{-1} v_j
+    const double *src = j == 0 ? cy.r0 : W.w;
+    const double *nrm2 = j == 0 ? cy.r0_nrm2 : W.redout + 3 * kMaxDots;
+    const double sc = j == 0 ? cy.r0_scale : 1.0;
+    PTROM_TIMED(PTROM_K_FOM_VEC, c.st, slots,
+                k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, src, sc, nrm2, W.D, c.hdt, c.transpose, vj, W.z, skip));
+    count_launch();
+    PTROM_TRY(apply_jvp(c, W.z, W.w, true, skip, slots));  // w = (I - hdt J) z
+    GivensArgs ga{W.gm, m, cy.r0_nrm2, cy.r0_scale, cy.first, c.p->gmres_rtol, cy.total + j + 1,
+                  c.p->gmres_max_iter, W.flags, W.stat + (1 + j) * kStatDoubles};
+    int K = j + 1;
     if (c.coop) {
         const double *V = W.V;
         double *w = W.w, *P = W.partials, *out = W.redout + kMaxDots;
-        void *args[] = {&n2, &K, &V, &w, &P, &out};
-        PTROM_CUDA(cudaLaunchCooperativeKernel((void *)k_cgs2, dim3(c.rgrid), dim3(kRedThreads), args, 0, c.st));
+        int n2v = n2;
+        void *args[] = {&n2v, &K, &V, &w, &P, &out, &ga, &skip};
+        cudaError_t e = cudaSuccess;
+        PTROM_TIMED(PTROM_K_FOM_ORTH, c.st, slots,
+                    e = cudaLaunchCooperativeKernel((void *)k_cgs2, dim3(c.rgrid), dim3(kRedThreads), args, 0, c.st));
+        PTROM_CUDA(e);
         count_launch();
-        return PTROM_OK;
+    } else {
+        PTROM_TIMED(PTROM_K_FOM_ORTH, c.st, slots,
+                    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.w, mkred(W, 1), skip);
+                    k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.redout + kMaxDots, W.w,
+                                                                      mkred(W, 3), skip);
+                    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.w, mkred(W, 2), skip);
+                    k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.redout + 2 * kMaxDots, W.w,
+                                                                      mkred(W, 3), skip);
+                    k_givens<<<1, 1, 0, c.st>>>(K, W.redout + kMaxDots, ga, skip));
+        count_launch(5);
     }
-    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.w, mkred(W, 1));
-    k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.redout + kMaxDots, W.w, mkred(W, 3));
-    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.w, mkred(W, 2));
-    k_orth_update<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, K, W.V, W.redout + 2 * kMaxDots, W.w, mkred(W, 3));
-    count_launch(4);
     PTROM_CUDA(cudaGetLastError());
-    return PTROM_OK;
+    return post(c, 1 + j);
 }
 
 // Solve (I - hdt J) d = rhs_scale * rhs with right-preconditioned GMRES(m),
-// M = blockdiag(I - hdt D_i).  rhs_nrm2: device address of ||rhs||^2 when the
-// caller has it (host value rhs_nrm2_host), else nullptr.  With x_upd given,
-// x_upd += d at the end (the Newton update).
-static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d, double *x_upd,
-                 const double *rhs_nrm2 = nullptr, double rhs_nrm2_host = 0.0) {
+// M = blockdiag(I - hdt D_i); d starts at 0.  rhs_nrm2: device ||rhs||^2.
+// With x_upd given, x_upd += d at the end (the Newton update).
+// queued: Arnoldi steps of the first cycle the caller has already queued
+// (0 or 1), with their timing slots in slots[].
+//
+// Pipelining: step j + 1 is queued before the host waits for step j's status,
+// so the GPU never waits for the host inside a cycle; when step j stops the
+// cycle, the queued step j + 1 runs as empty kernels and its timing slot is
+// dropped.
+static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d, double *x_upd, const double *rhs_nrm2,
+                 int queued = 0, const Slots *first = nullptr) {
     const int n2 = c.n2, m = c.p->gmres_restart;
     Work &W = c.W;
-    PTROM_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n2, c.st));
-    if (!rhs_nrm2) {
-        k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, rhs, mkred(W, 0));
-        count_launch();
-        PTROM_TRY(fetch(c, W.redout, &rhs_nrm2_host, 1));
-        rhs_nrm2 = W.redout;
-    }
-    const double bnorm = fabs(rhs_scale) * sqrt(rhs_nrm2_host);
-    if (bnorm == 0.0) return PTROM_OK;
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hbuf(3 * kMaxDots);
-    double *hdev = W.redout + kMaxDots;  // slots 1..3: h (two passes), ||w||^2
-    int total = 0;
-    const double *r0 = rhs;  // first cycle: r0 = b (d = 0)
-    double r0_scale = rhs_scale;
-    const double *r0_nrm2 = rhs_nrm2;
-    double beta = bnorm;
+    std::vector<Slots> tslot(m + 1);
+    if (queued && first) tslot[0] = *first;
+    Cycle cy{rhs, rhs_scale, rhs_nrm2, 1, 0};
+    double bnorm = 0.0;
     while (true) {
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int jl = -1;
+        int next = queued;
+        if (next == 0) PTROM_TRY(queue_step(c, cy, next++, &tslot[0]));
+        int K = m;
         bool done = false;
         for (int j = 0; j < m; ++j) {
-            double *vj = W.V + (size_t)j * n2;
-            // v_j = previous Krylov vector / its norm (read on the device); z = M^{-1} v_j
-            if (j == 0)
-                k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, r0, r0_scale, r0_nrm2, W.D, c.hdt, c.transpose, vj, W.z);
-            else
-                k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, W.w, 1.0, hdev + 2 * kMaxDots, W.D, c.hdt, c.transpose,
-                                                          vj, W.z);
-            count_launch();
-            PTROM_TRY(apply_jvp(c, W.z, W.w, true));  // w = (I - hdt J) z
-            PTROM_TRY(cgs2(c, j + 1));
-            PTROM_TRY(fetch(c, hdev, hbuf.data(), 2 * kMaxDots + 1));
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hbuf[i] + hbuf[kMaxDots + i];
-            const double hn = sqrt(hbuf[2 * kMaxDots]);
-            H[(size_t)(j + 1) * m + j] = hn;
-            if (!isfinite(hn)) return set_error(PTROM_ENAN, "fom: non-finite Krylov vector");
-            // Givens
-            for (int i = 0; i < j; ++i) {
-                const double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
-                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b2;
-                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b2;
+            if (next == j + 1 && next < m) {
+                PTROM_TRY(queue_step(c, cy, next, &tslot[next]));
+                ++next;
             }
-            const double a = H[(size_t)j * m + j], b2 = H[(size_t)(j + 1) * m + j];
-            const double rr = hypot(a, b2);
-            cs[j] = rr > 0 ? a / rr : 1.0;
-            sn[j] = rr > 0 ? b2 / rr : 0.0;
-            H[(size_t)j * m + j] = rr;
-            H[(size_t)(j + 1) * m + j] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            ++total;
-            jl = j;
-            if (c.stats) c.stats->linear_iters++;
-            if (fabs(g[j + 1]) <= c.p->gmres_rtol * bnorm || total >= c.p->gmres_max_iter || hn == 0.0) {
+            const double *st = wait_post(c, 1 + j);
+            if (!st) return set_error(PTROM_ECUDA, "fom: waiting for GMRES step %d failed", j);
+            if (c.stats) {
+                c.stats->jvp_evals++;
+                c.stats->linear_iters++;
+            }
+            bnorm = st[3];
+            if (st[0] == 2.0) return set_error(PTROM_ENAN, "fom: non-finite Krylov vector");
+            if (st[0] != 0.0) {
+                K = j + 1;
                 done = true;
                 break;
             }
         }
-        // y = R^{-1} g;  d += M^{-1} V y  (and x += d after the last cycle)
-        const int K = jl + 1;
-        for (int i = K - 1; i >= 0; --i) {
-            double s = g[i];
-            for (int k = i + 1; k < K; ++k) s -= H[(size_t)i * m + k] * y[k];
-            y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
-        }
-        Coef cf{};
-        for (int k = 0; k < K; ++k) cf.y[k] = y[k];
-        k_combine_precond<<<c.grid, 256, 0, c.st>>>(c.n, K, W.V, cf, W.D, c.hdt, c.transpose, d,
-                                                     done ? x_upd : nullptr);
+        for (int j = K; j < next; ++j) discard(tslot[j]);  // queued steps that did nothing
+        for (auto &t : tslot) t.n = 0;
+        queued = 0;
+        PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                    k_combine_precond<<<c.grid, 256, 0, c.st>>>(c.n, K, m, W.V, W.gm, W.D, c.hdt, c.transpose, d,
+                                                                 done ? x_upd : nullptr));
         count_launch();
         PTROM_CUDA(cudaGetLastError());
         if (done) break;
         // restart: r0 = b - (I - hdt J) d
         PTROM_TRY(apply_jvp(c, d, W.jz, true));
-        k_restart_res<<<c.grid, 256, 0, c.st>>>(n2, rhs, rhs_scale, W.jz, W.b);
-        k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, W.b, mkred(W, 0));
+        if (c.stats) c.stats->jvp_evals++;
+        PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                    k_restart_res<<<c.grid, 256, 0, c.st>>>(n2, rhs, rhs_scale, W.jz, W.b);
+                    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(n2, 1, nullptr, W.b, mkred(W, 0)));
         count_launch(2);
         double r2 = 0.0;
         PTROM_TRY(fetch(c, W.redout, &r2, 1));
-        beta = sqrt(r2);
-        if (beta <= c.p->gmres_rtol * bnorm) {
+        if (sqrt(r2) <= c.p->gmres_rtol * bnorm) {
             if (x_upd) {
                 k_axpy<<<c.grid, 256, 0, c.st>>>(n2, 1.0, d, x_upd);
                 count_launch();
             }
             break;
         }
-        r0 = W.b;
-        r0_scale = 1.0;
-        r0_nrm2 = W.redout;
+        cy = Cycle{W.b, 1.0, W.redout, 0, cy.total + m};
+        PTROM_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(int), c.st));
     }
     return PTROM_OK;
 }
@@ -755,42 +916,58 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
     if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
     c.rgrid = red_grid(c.n2);
     c.coop = cgs2_coop_fits(c.rgrid);
+    PTROM_TRY(host_mailbox(kStatSlots * kStatDoubles, kStatSlots, &c.mb, &c.ev));
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;
     memset(c.stats, 0, sizeof(*c.stats));
     Work &W = c.W;
     PTROM_CUDA(cudaMemsetAsync(W.counter, 0, 64, c.st));
+    PTROM_CUDA(cudaMemsetAsync(W.flags, 0, 64, c.st));
     PTROM_CUDA(cudaMemcpyAsync(W.xprev, x, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
     PTROM_CUDA(cudaMemcpyAsync(W.fprev, f, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
     bool have_jac = false;
     for (int k = 0; k <= p->max_iter; ++k) {
         const bool refresh = (k % p->p_it == 0) || !have_jac;
-        PTROM_TRY(velocity(n, x, n, x, Gamma, p->delta, W.fxi, refresh ? W.D : nullptr, p->prec, c.st, 0,
-                           W.pack));
+        LaunchOpts vo;
+        vo.scratch = W.pack;
+        PTROM_TRY(velocity(n, x, n, x, Gamma, p->delta, W.fxi, refresh ? W.D : nullptr, p->prec, c.st, vo));
         c.stats->velocity_evals++;
-        k_residual<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, x, W.xprev, W.fxi, W.fprev, c.hdt, W.r, mkred(W, 0));
+        PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                    k_residual<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, x, W.xprev, W.fxi, W.fprev, c.hdt, W.r,
+                                                                 mkred(W, 0), p->tol, k == p->max_iter, W.flags,
+                                                                 W.stat));
         count_launch();
         PTROM_CUDA(cudaGetLastError());
-        double nr[2];
-        PTROM_TRY(fetch(c, W.redout, nr, 2));
-        const double rn = sqrt(nr[0]), xn = sqrt(nr[1]);
+        PTROM_TRY(post(c, 0));
+        // JFNK: queue the first Arnoldi step before reading the Newton test
+        // (it skips itself if the test stops the iteration)
+        Slots slot0;
+        const bool jfnk = p->jac_mode == PTROM_JAC_JFNK;
+        if (jfnk) {
+            PTROM_CUDA(cudaMemsetAsync(W.d, 0, sizeof(double) * c.n2, c.st));
+            const Cycle cy{W.r, -1.0, W.redout, 1, 0};
+            PTROM_TRY(queue_step(c, cy, 0, &slot0));
+        }
+        const double *st = wait_post(c, 0);
+        if (!st) return set_error(PTROM_ECUDA, "fom_step: waiting for the residual failed");
+        const int stop = (int)st[0];
+        const double rn = st[1];
         if (k == 0) c.stats->res_norm0 = rn;
         c.stats->res_norm = rn;
-        if (!isfinite(rn)) return set_error(PTROM_ENAN, "fom_step: non-finite residual at iteration %d", k);
-        const bool conv = rn <= p->tol * (xn > 1.0 ? xn : 1.0);
-        if (conv || k == p->max_iter) {
+        if (stop != 0) {
+            discard(slot0);
+            if (stop == 2) return set_error(PTROM_ENAN, "fom_step: non-finite residual at iteration %d", k);
             PTROM_CUDA(cudaMemcpyAsync(f, W.fxi, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
-            if (!conv)
-                return set_error(PTROM_ENOCONV, "fom_step: %d Newton iterations, |r| = %.3e", k, rn);
+            if (stop == 3) return set_error(PTROM_ENOCONV, "fom_step: %d Newton iterations, |r| = %.3e", k, rn);
             return PTROM_OK;
         }
         c.stats->newton_iters++;
         if (p->jac_mode == PTROM_JAC_BLOCKDIAG) {
             k_blockdiag<<<c.grid, 256, 0, c.st>>>(n, W.D, W.r, c.hdt, -1.0, x, 1, 0);
             count_launch();
-        } else if (p->jac_mode == PTROM_JAC_JFNK) {
+        } else if (jfnk) {
             // solve (I - hdt J) d = -r; x += d (slot 0 of redout holds ||r||^2)
-            PTROM_TRY(gmres(c, W.r, -1.0, W.d, x, W.redout, nr[0]));
+            PTROM_TRY(gmres(c, W.r, -1.0, W.d, x, W.redout, 1, &slot0));
         } else {
             if (refresh) PTROM_TRY(dense_factor(c));
             k_lu_solve<<<1, 1024, 0, c.st>>>(c.n2, W.M, W.perm, W.r, -1.0, W.d);
@@ -858,22 +1035,31 @@ extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *
     if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
     c.rgrid = red_grid(c.n2);
     c.coop = cgs2_coop_fits(c.rgrid);
+    PTROM_TRY(host_mailbox(kStatSlots * kStatDoubles, kStatSlots, &c.mb, &c.ev));
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;
     memset(c.stats, 0, sizeof(*c.stats));
     Work &W = c.W;
     PTROM_CUDA(cudaMemsetAsync(W.counter, 0, 64, c.st));
+    PTROM_CUDA(cudaMemsetAsync(W.flags, 0, 64, c.st));
     // self blocks at x^n for the (transposed) preconditioner
-    PTROM_TRY(velocity(n, x_n, n, x_n, Gamma, q.delta, W.fxi, W.D, q.prec, c.st, 0, W.pack));
+    LaunchOpts po;
+    po.scratch = W.pack;
+    PTROM_TRY(velocity(n, x_n, n, x_n, Gamma, q.delta, W.fxi, W.D, q.prec, c.st, po));
     c.stats->velocity_evals++;
-    // mu = (I - h J_n)^{-T} lambda
-    PTROM_TRY(gmres(c, lambda, 1.0, W.d, nullptr));
+    // mu = (I - h J_n)^{-T} lambda  (mu = 0 when lambda = 0)
+    PTROM_CUDA(cudaMemsetAsync(W.d, 0, sizeof(double) * c.n2, c.st));
+    k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, 1, nullptr, lambda, mkred(W, 0));
+    count_launch();
+    double l2 = 0.0;
+    PTROM_TRY(fetch(c, W.redout, &l2, 1));
+    if (l2 > 0.0) PTROM_TRY(gmres(c, lambda, 1.0, W.d, nullptr, W.redout));
     // gGamma += h F_n^T mu
-    PTROM_TRY(vjp(n, x_n, Gamma, q.delta, W.d, nullptr, gtmp, q.prec, c.st, 0, W.pack));
+    PTROM_TRY(vjp(n, x_n, Gamma, q.delta, W.d, nullptr, gtmp, q.prec, c.st, po));
     k_axpy<<<c.grid, 256, 0, c.st>>>(n, c.hdt, gtmp, gGamma);
     count_launch();
     // lambda_prev = mu + h J_{n-1}^T mu ;  gGamma += h F_{n-1}^T mu
-    PTROM_TRY(vjp(n, x_prev, Gamma, q.delta, W.d, W.jz, gtmp, q.prec, c.st, 0, W.pack));
+    PTROM_TRY(vjp(n, x_prev, Gamma, q.delta, W.d, W.jz, gtmp, q.prec, c.st, po));
     c.stats->jvp_evals += 2;
     k_axpby<<<c.grid, 256, 0, c.st>>>(c.n2, 1.0, W.d, c.hdt, W.jz, lambda);
     k_axpy<<<c.grid, 256, 0, c.st>>>(n, c.hdt, gtmp, gGamma);

@@ -13,15 +13,35 @@ struct LinEpi {
     double hdt = 0.0;
 };
 
-// All-pairs launches (bs_pair.cu).  split = 0 -> automatic cluster split.
-// scratch: device buffer of at least pack_scratch_bytes(ns) bytes for the
-// packed sources, or nullptr (stream-ordered allocation from the pool).
+// Options of one all-pairs launch (bs_pair.cu):
+//   split   0 -> automatic cluster split, S in 1..8 -> forced;
+//   scratch device buffer of at least pack_scratch_bytes(ns) bytes for the
+//           packed sources, or nullptr (stream-ordered allocation from the pool);
+//   lin     J v / J^T w only: the (I - hdt J) epilogue;
+//   skip    optional device flag: nonzero at launch -> the launch does nothing;
+//   slots   optional: collects the launches' timing slots (so a launch that
+//           turned out to be skipped can be left out of the timing totals).
+struct Slots {
+    int s[16];
+    int n = 0;
+    void add(int v) {
+        if (v >= 0 && n < 16) s[n++] = v;
+    }
+};
+struct LaunchOpts {
+    int split = 0;
+    void *scratch = nullptr;
+    LinEpi lin;
+    const int *skip = nullptr;
+    Slots *slots = nullptr;
+};
+
 int velocity(int nt, const double *xt, int ns, const double *xs, const double *G, double delta,
-             double *f, double *D, int prec, cudaStream_t st, int split, void *scratch = nullptr);
+             double *f, double *D, int prec, cudaStream_t st, const LaunchOpts &o = {});
 int jvp(int n, const double *x, const double *G, double delta, const double *v, double *jv,
-        int prec, cudaStream_t st, int split, void *scratch = nullptr, LinEpi lin = LinEpi{});
+        int prec, cudaStream_t st, const LaunchOpts &o = {});
 int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
-        double *gG, int prec, cudaStream_t st, int split, void *scratch = nullptr, LinEpi lin = LinEpi{});
+        double *gG, int prec, cudaStream_t st, const LaunchOpts &o = {});
 size_t pack_scratch_bytes(int ns);
 // Batched velocity (+ self blocks when D != nullptr) over B instances; S = source split.
 int velocity_batched(int B, const int *n, const double *const *x, const double *const *G, const double *delta,

@@ -71,5 +71,7 @@ extern "C" int bs_velocity_noalloc(int nt, const double *xt, int ns, const doubl
     // The pack kernel rewrites every record the pair kernel reads (all
     // ceil(ns/32)*32 of them, padding included) before it is read, so nothing
     // in the array needs clearing between calls.
-    return velocity(nt, xt, ns, xs, Gamma, delta, f_out, selfjac_out, prec, (cudaStream_t)stream, 0, scratch);
+    LaunchOpts o;
+    o.scratch = scratch;
+    return velocity(nt, xt, ns, xs, Gamma, delta, f_out, selfjac_out, prec, (cudaStream_t)stream, o);
 }

@@ -15,8 +15,8 @@
 //     shared-memory double buffer (coalesced 16-byte loads of the next chunk are
 //     in flight while the current one is consumed), so no CTA-wide barrier
 //     sits in the loop;
-//   * gridDim.y splits the sources further; the gridDim.y CTAs of one target
-//     block form a thread-block cluster and reduce their partial sums through
+//   * gridDim.y (default 4) splits the sources further; the gridDim.y CTAs
+//     of one target block form a thread-block cluster and reduce their partial sums through
 //     distributed shared memory in a fixed order (deterministic, no atomics,
 //     no global scratch).
 // Accumulation: FP32 pair terms summed plainly inside a chunk, then folded
@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace ptrom {
 namespace cg = cooperative_groups;
@@ -39,6 +40,11 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kChunk = 32;
 constexpr int kTB = 64;
 constexpr int kMaxCluster = 8;
+constexpr int kAutoSplit = 4;  // default source split (cluster size)
+#ifndef PTROM_PAIR_UNROLL
+#define PTROM_PAIR_UNROLL 8
+#endif
+constexpr int kPairUnroll = PTROM_PAIR_UNROLL;  // unroll of the per-chunk source loop
 
 // ---- 2-wide vector traits: FP32 (packed instructions) or FP64 -----------------
 template <typename T> struct VT;
@@ -107,9 +113,12 @@ __device__ __forceinline__ V mask_zero(V q, V d2) {
 //   load_tgt(args, t0, t1, Origin, Tgt&) t >= nt -> harmless padding
 //   pair(const Rec&, Tgt&, V part[NACC])  add one source's contribution
 //   finalize(args, t, const double s[NACC])  write target t's outputs
+// skip: optional device flag; when it is nonzero at launch the kernel does
+// nothing (a speculatively queued launch whose result is not needed).
 template <class Op>
 __global__ void __launch_bounds__(256)
-pack_kernel(const typename Op::Args args, typename Op::Rec *__restrict__ out, int ns_pad) {
+pack_kernel(const typename Op::Args args, typename Op::Rec *__restrict__ out, int ns_pad, const int *skip) {
+    if (skip && *skip) return;
     const typename Op::Origin org = Op::origin(args);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns_pad; j += gridDim.x * blockDim.x)
         out[j] = Op::pack(args, j, org);
@@ -160,7 +169,7 @@ __device__ __forceinline__ void pair_block(const typename Op::Args &args, const 
         V part[NACC];
 #pragma unroll
         for (int k = 0; k < NACC; ++k) part[k] = VT<R>::mk(0, 0);
-#pragma unroll 8
+#pragma unroll kPairUnroll
         for (int k = 0; k < kChunk; ++k) Op::pair(stage[warp][b].r[k], tgt, part);
 #pragma unroll
         for (int k = 0; k < NACC; ++k) acc[k].add(part[k]);
@@ -218,7 +227,8 @@ __device__ __forceinline__ void pair_block(const typename Op::Args &args, const 
 
 template <class Op>
 __global__ void __launch_bounds__(kThreads, Op::kMinBlocks)
-pair_kernel(const typename Op::Args args, const typename Op::Rec *__restrict__ packed, int nchunks) {
+pair_kernel(const typename Op::Args args, const typename Op::Rec *__restrict__ packed, int nchunks, const int *skip) {
+    if (skip && *skip) return;  // uniform over the grid: no CTA reaches a cluster barrier
     pair_block<Op>(args, packed, nchunks, blockIdx.x * kTB);
 }
 
@@ -264,37 +274,27 @@ pack_kernel_batched(const BatchItem<Op> *__restrict__ items, const int *__restri
 
 // Launch helper: packs the sources (into `scratch` when given, else into a
 // stream-ordered allocation freed right after), picks the cluster split S
-// (1..8) that best fills the GPU's CTA slots, and launches the pair kernel.
+// (1..8) and launches the pair kernel.
 template <class Op>
-int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t stream, int force_split = 0,
-                 void *scratch = nullptr) {
+int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t stream, const LaunchOpts &o = {}) {
+    const int force_split = o.split;
+    void *scratch = o.scratch;
     using Rec = typename Op::Rec;
     const int tblocks = (nt + kTB - 1) / kTB;
     const int nchunks = (ns + kChunk - 1) / kChunk;
     const int ns_pad = nchunks * kChunk;
     int S = 1;
-    if (force_split <= 0) force_split = g_source_split.load();
-    if (force_split > 0) {
-        S = force_split;
+    const int forced = force_split > 0 ? force_split : g_source_split.load();
+    if (forced > 0) {
+        S = forced;
     } else {
-        // resident CTAs per SM from the kernel's registers / shared memory
-        static int per_sm = 0;
-        if (per_sm == 0) {
-            int v = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, pair_kernel<Op>, kThreads, 0) != cudaSuccess || v < 1)
-                v = Op::kMinBlocks;
-            per_sm = v;
-        }
-        const int slots = per_sm * device_sm_count();
-        double best = -1.0;
-        for (int s = 1; s <= kMaxCluster; ++s) {
-            if (s > 1 && nchunks < s * kWarps) break;  // keep every warp busy
-            const long long ctas = (long long)tblocks * s;
-            const long long waves = (ctas + slots - 1) / slots;
-            // fraction of CTA slots used over the waves, mildly favouring fewer splits
-            const double eff = (double)ctas / (double)(waves * slots) - 0.01 * s;
-            if (eff > best + 1e-9) { best = eff; S = s; }
-        }
+        // kAutoSplit CTAs per target block, fewer when the warps would run out
+        // of chunks: measured on GB300 at N = 4096 .. 65536, a split of 4 is
+        // within a few per cent of the best split for every op, while larger
+        // splits (more, shorter CTAs that fill the last wave) lose more to the
+        // per-CTA prologue and cluster reduction than they gain.
+        S = kAutoSplit;
+        while (S > 1 && nchunks < S * kWarps) --S;
     }
     if (S < 1 || S > kMaxCluster) return set_error(PTROM_EINVAL, "bad source split %d", S);
     Rec *packed = reinterpret_cast<Rec *>(scratch);
@@ -302,7 +302,10 @@ int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t str
     if (own) PTROM_TRY(scratch_alloc((void **)&packed, sizeof(Rec) * (size_t)ns_pad, stream));
     int pgrid = (ns_pad + 255) / 256;
     if (pgrid > 4 * device_sm_count()) pgrid = 4 * device_sm_count();
-    pack_kernel<Op><<<pgrid, 256, 0, stream>>>(args, packed, ns_pad);
+    const int pslot = timing_begin(PTROM_K_PACK, stream);
+    pack_kernel<Op><<<pgrid, 256, 0, stream>>>(args, packed, ns_pad, o.skip);
+    timing_end(pslot, stream);
+    if (o.slots) o.slots->add(pslot);
     count_launch();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(tblocks, S, 1);
@@ -317,8 +320,9 @@ int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t str
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int slot = timing_begin(Op::kKind, stream);
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, pair_kernel<Op>, args, (const Rec *)packed, nchunks);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, pair_kernel<Op>, args, (const Rec *)packed, nchunks, o.skip);
     timing_end(slot, stream);
+    if (o.slots) o.slots->add(slot);
     if (own) {
         const int s2 = scratch_free(packed, stream);
         if (e == cudaSuccess && s2 != PTROM_OK) return s2;

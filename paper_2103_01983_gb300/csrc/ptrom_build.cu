@@ -675,7 +675,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     for (int q = 0; q < n_params; ++q) {
         const double *x0 = x0s + (size_t)q * nd, *G = gammas + (size_t)q * n;
         PTROM_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * nd, cudaMemcpyDeviceToDevice, st));
-        PTROM_TRY(velocity(n, x, n, x, G, delta, f, nullptr, p->fom.prec, st, 0));
+        PTROM_TRY(velocity(n, x, n, x, G, delta, f, nullptr, p->fom.prec, st));
         for (int s = 0; s < p->steps; ++s) {
             const int stt = fom_step(&p->fom, n, G, x, f, work, wbytes, nullptr, stream);
             if (stt != PTROM_OK && stt != PTROM_ENOCONV) return stt;

@@ -73,7 +73,8 @@ static size_t g_used = 0;
 constexpr size_t kMaxTimed = 65536;
 
 int timing_begin(int kind, cudaStream_t st) {
-    if (!g_timing.load(std::memory_order_relaxed)) return -1;
+    const int mask = g_timing.load(std::memory_order_relaxed);
+    if (!mask || kind < 0 || kind >= 31 || !(mask & (1 << kind))) return -1;
     std::lock_guard<std::mutex> lk(g_tmu);
     if (g_used >= kMaxTimed) return -1;
     while (g_ev.size() < 2 * (g_used + 1)) {
@@ -93,12 +94,53 @@ void timing_end(int slot, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_tmu);
     cudaEventRecord(g_ev[2 * slot + 1], st);
 }
+
+void timing_discard(int slot) {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if ((size_t)slot < g_used && (size_t)slot < g_kind.size()) g_kind[slot] = -1;
+}
+
+namespace {
+struct Mailbox {
+    double *host = nullptr;
+    size_t n = 0;
+    std::vector<cudaEvent_t> ev;
+    ~Mailbox() {
+        if (host) cudaFreeHost(host);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+thread_local Mailbox t_mailbox[64];
+}  // namespace
+
+int host_mailbox(size_t ndoubles, int nevents, double **host, cudaEvent_t **events) {
+    int dev = 0;
+    PTROM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(PTROM_EINVAL, "host_mailbox: device %d out of range", dev);
+    Mailbox &mb = t_mailbox[dev];
+    if (mb.n < ndoubles) {
+        if (mb.host) cudaFreeHost(mb.host);
+        mb.host = nullptr;
+        mb.n = 0;
+        PTROM_CUDA(cudaHostAlloc((void **)&mb.host, sizeof(double) * ndoubles, cudaHostAllocDefault));
+        mb.n = ndoubles;
+    }
+    while ((int)mb.ev.size() < nevents) {
+        cudaEvent_t e;
+        PTROM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        mb.ev.push_back(e);
+    }
+    *host = mb.host;
+    *events = mb.ev.data();
+    return PTROM_OK;
+}
 }  // namespace ptrom
 
 extern "C" long long ptrom_launch_count(void) { return ptrom::g_launches.load(); }
 
 extern "C" int ptrom_timing_enable(int on) {
-    ptrom::g_timing.store(on ? 1 : 0);
+    ptrom::g_timing.store(on == 1 ? 0x7fffffff : (on > 0 ? on : 0));
     return PTROM_OK;
 }
 

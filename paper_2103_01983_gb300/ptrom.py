@@ -182,7 +182,8 @@ def _prec(p):
         raise ValueError(f"prec must be 'fp32c' or 'fp64', got {p!r}") from None
 
 
-KERNEL_KINDS = ["velocity", "velocity_selfjac", "jvp", "vjp", "jphi", "ptrom_step"]
+KERNEL_KINDS = ["velocity", "velocity_selfjac", "jvp", "vjp", "jphi", "ptrom_step", "pack", "fom_vec",
+                "fom_orth"]
 
 
 def launch_count() -> int:
@@ -190,8 +191,18 @@ def launch_count() -> int:
     return int(lib.ptrom_launch_count())
 
 
-def timing_enable(on: bool) -> None:
-    lib.ptrom_timing_enable(1 if on else 0)
+def timing_enable(on, kinds=None) -> None:
+    """Start (on) or stop event timing; kinds: optional names from KERNEL_KINDS
+    to time (default: all)."""
+    if not on:
+        lib.ptrom_timing_enable(0)
+    elif kinds is None:
+        lib.ptrom_timing_enable(1)
+    else:
+        mask = 0
+        for k in kinds:
+            mask |= 1 << KERNEL_KINDS.index(k)
+        lib.ptrom_timing_enable(mask if mask != 1 else 1 | (1 << 30))
 
 
 def timing_read() -> dict:

@@ -125,3 +125,47 @@ def test_full_size_step_residual_sampled(P):
         assert rel_f <= 1e-5
         np.testing.assert_allclose(qoi.linear_impulse(xn, G), qoi.linear_impulse(x0, G), atol=1e-9)
         xp = xn
+
+
+@pytest.mark.parametrize("restart", [1, 2, 3])
+def test_jfnk_short_restart_cycles_fp64(P, restart):
+    """GMRES(m) with m = 1..3 and a tight tolerance runs several cycles per
+    Newton iteration (restart residual, device least squares of every cycle,
+    the pipelined Arnoldi steps); the trajectory still matches the oracle."""
+    x0, G = W.disk(300, seed=3)
+    params = P.fom_params(0.01, 0.05, "jfnk", tol=1e-13, prec="fp64", gmres_restart=restart,
+                          gmres_rtol=1e-10, gmres_max_iter=400)
+    traj, stats, _ = _gpu_rollout(P, x0, G, params, 3, "fp64")
+    ref, _ = fom.rollout(x0, G, 0.05, 0.01, 3, mode="dense", tol=1e-14)
+    assert np.abs(traj - ref).max() <= 1e-11
+    for s in stats:
+        # more Krylov steps than one cycle holds: restarts happened
+        assert s["linear_iters"] > restart * s["newton_iters"]
+        # every counted J v is an Arnoldi step or a restart residual
+        assert s["linear_iters"] <= s["jvp_evals"] <= 2 * s["linear_iters"]
+
+
+def test_jfnk_iteration_cap_and_counts(P):
+    """gmres_max_iter caps the Krylov steps per solve; the counts the host
+    reports are the steps that ran (steps queued ahead and skipped are not
+    counted) and the library's event timing holds only those launches."""
+    x0, G = W.two_cluster(1024, seed=2)
+    x, Gt = _dev(x0), _dev(G)
+    capped = P.fom_params(0.005, 0.02, "jfnk", prec="fp64", tol=1e-6, gmres_rtol=1e-14, gmres_max_iter=3)
+    f = P.bs_velocity(x, Gt, 0.02, prec="fp64")
+    st = P.fom_step(capped, Gt, x, f, allow_noconv=True)
+    assert st["linear_iters"] <= 3 * st["newton_iters"]
+    params = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c")
+    x, f = _dev(x0), P.bs_velocity(_dev(x0), Gt, 0.02)
+    work = P.fom_workspace(params, 1024)
+    P.timing_read()
+    P.timing_enable(True)
+    try:
+        st = P.fom_step(params, Gt, x, f, work=work)
+        torch.cuda.synchronize()
+        t = P.timing_read()
+    finally:
+        P.timing_enable(False)
+    assert st["newton_iters"] >= 1 and st["linear_iters"] >= st["newton_iters"]
+    assert t["jvp"][1] == st["jvp_evals"]
+    assert t["velocity"][1] + t["velocity_selfjac"][1] == st["velocity_evals"]
