@@ -125,6 +125,15 @@ __global__ void k_residual(int n2, const double *xi, const double *xprev, const 
 // (at most kMaxPer per thread), warps reduce every dot by shuffles, one CTA
 // barrier combines the warps.
 constexpr int kMaxPer = 8;
+constexpr int kMaxB = kMaxPer / 2;  // bodies per thread in the cooperative FOM kernels (at most)
+constexpr int kCoopBodies = 2;      // bodies per thread the cooperative grids are sized for
+// Cooperative grid for n bodies: few blocks keep the grid barriers and the
+// per-block partial sums cheap (the vectors are small; latency, not
+// bandwidth, bounds these kernels).
+static int coop_grid(int n) {
+    const int g = (n + kRedThreads * kCoopBodies - 1) / (kRedThreads * kCoopBodies);
+    return g < 1 ? 1 : g;
+}
 __global__ void k_multidot(int n2, int K, const double *V, const double *w, Red red, const int *skip = nullptr) {
     if (skip && *skip) return;
     __shared__ double sh[kRedThreads / 32][kMaxDots];
@@ -186,6 +195,35 @@ __device__ __forceinline__ void bd_solve(const double *D, int n, int i, double h
     z1 = scale * (m00 * r1 - m10 * r0) / det;
 }
 
+// The preconditioner as stored inverse blocks: Mi = [a | b | c | d] (4 n
+// doubles), M_i^{-1} = [[a, b], [c, d]] = (I - hdt D_i)^{-1}, built once per
+// refresh of D so that applying it is four multiply-adds (FP64 division is
+// slow on GB300 and sat on the latency path of every small FOM kernel).
+__device__ __forceinline__ void minv_fill(const double *D, double *Mi, int n, int i, double hdt) {
+    const double d00 = D[i], d01 = D[n + i], d10 = D[2 * n + i], d11 = -d00;
+    const double m00 = 1.0 - hdt * d00, m01 = -hdt * d01, m10 = -hdt * d10, m11 = 1.0 - hdt * d11;
+    const double inv = 1.0 / (m00 * m11 - m01 * m10);
+    Mi[i] = m11 * inv;
+    Mi[n + i] = -m01 * inv;
+    Mi[2 * (size_t)n + i] = -m10 * inv;
+    Mi[3 * (size_t)n + i] = m00 * inv;
+}
+// z = M_i^{-1} r (M_i^{-T} r when transpose is set)
+__device__ __forceinline__ void minv_apply(const double *Mi, int n, int i, int transpose, double r0, double r1,
+                                           double &z0, double &z1) {
+    const double a = Mi[i], b = Mi[n + i], c = Mi[2 * (size_t)n + i], d = Mi[3 * (size_t)n + i];
+    if (transpose) {
+        z0 = a * r0 + c * r1;
+        z1 = b * r0 + d * r1;
+    } else {
+        z0 = a * r0 + b * r1;
+        z1 = c * r0 + d * r1;
+    }
+}
+__global__ void k_minv(int n, const double *D, double hdt, double *Mi) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) minv_fill(D, Mi, n, i, hdt);
+}
+
 // Block-diagonal solve: z_i = scale * (I - hdt D_i)^{-1} v_i, added to z
 // when accumulate is set.
 __global__ void k_blockdiag(int n, const double *D, const double *v, double hdt, double scale,
@@ -206,16 +244,16 @@ __global__ void k_blockdiag(int n, const double *D, const double *v, double hdt,
 // Next Arnoldi vector and its preconditioned image in one pass:
 //   v = scale * src / (|scale| sqrt(*nrm2))  -> V_out,   z = M^{-1} v
 // (*nrm2 = ||src||^2 on the device, so the host need not read it first).
-__global__ void k_norm_precond(int n, const double *src, double scale, const double *nrm2, const double *D,
-                               double hdt, int transpose, double *V_out, double *z, const int *skip) {
-    if (*skip) return;
+__global__ void k_norm_precond(int n, const double *src, double scale, const double *nrm2, const double *Mi,
+                               int transpose, double *V_out, double *z, const int *skip) {
+    if (skip && *skip) return;
     const double inv = 1.0 / (fabs(scale) * sqrt(*nrm2));
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double v0 = inv * (scale * src[i]), v1 = inv * (scale * src[n + i]);
         V_out[i] = v0;
         V_out[n + i] = v1;
         double z0, z1;
-        bd_solve(D, n, i, hdt, transpose, v0, v1, 1.0, z0, z1);
+        minv_apply(Mi, n, i, transpose, v0, v1, z0, z1);
         z[i] = z0;
         z[n + i] = z1;
     }
@@ -279,8 +317,8 @@ __device__ void givens_column(GmDev gm, int m, int j, const double *h1, const do
 // K x K block of the rotated H; each block solves it, warp 0, in shared
 // memory), then d += M^{-1} (sum_k y_k V_k); with x given, also x += d (the
 // Newton update after the last cycle).
-__global__ void k_combine_precond(int n, int K, int m, const double *V, GmDev gm, const double *D, double hdt,
-                                  int transpose, double *d, double *x) {
+__global__ void k_combine_precond(int n, int K, int m, const double *V, GmDev gm, const double *Mi, int transpose,
+                                  double *d, double *x) {
     __shared__ double y[kMaxRestart];
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -304,7 +342,7 @@ __global__ void k_combine_precond(int n, int K, int m, const double *V, GmDev gm
             u1 += y[k] * V[k * n2 + n + i];
         }
         double z0, z1;
-        bd_solve(D, n, i, hdt, transpose, u0, u1, 1.0, z0, z1);
+        minv_apply(Mi, n, i, transpose, u0, u1, z0, z1);
         const double d0 = d[i] + z0, d1 = d[n + i] + z1;
         d[i] = d0;
         d[n + i] = d1;
@@ -321,15 +359,7 @@ __global__ void k_restart_res(int n2, const double *rhs, double scale, const dou
         r0[i] = scale * rhs[i] - a[i];
 }
 
-// Classical Gram-Schmidt applied twice to w against V_0..V_{K-1}, as one
-// cooperative kernel: each thread keeps its (at most kMaxPer) entries of w in
-// registers through both passes.  Per pass: block partial dots -> grid
-// barrier -> every block sums the partials in the same fixed order (so all
-// blocks hold identical coefficients) -> w -= sum_k h_k V_k.  Outputs:
-// out[0..K) = first-pass h, out[kMaxDots..) = second-pass h,
-// out[2 kMaxDots] = ||w||^2 after both passes; w is written back.  Block 0
-// then adds the column to the least squares (givens_column, arguments G).
-// partials: 2 * gridDim.x * kMaxDots + gridDim.x doubles.
+// Arguments of givens_column for one Arnoldi step.
 struct GivensArgs {
     GmDev gm;
     int m;
@@ -341,89 +371,275 @@ struct GivensArgs {
     int *flags;
     double *st;
 };
+
+// Classical Gram-Schmidt applied twice to w against V_0..V_{K-1}, as one
+// cooperative kernel over bodies: each thread keeps both components of its
+// (at most kMaxB) bodies of w in registers throughout.  Per pass: block
+// partial dots -> grid barrier -> every block sums the partials in the same
+// fixed order (all blocks hold identical coefficients) -> w -= sum_k h_k V_k.
+// The second pass also sums ||w||^2 before its update, so the final norm is
+// ||w||^2 - sum_k h2_k^2 (Pythagoras, V orthonormal) without a third
+// reduction; when that subtraction loses more than half of ||w||^2 the norm is
+// summed again exactly (a uniform branch: every block sees the same values).
+// Outputs: out[0..K) first-pass h, out[kMaxDots..) second-pass h,
+// out[2 kMaxDots] = ||w||^2; block 0 adds the column to the least squares
+// (givens_column).  Finally every block writes the next Arnoldi vector
+// v = w / ||w|| (Vnext) and its preconditioned image z = M^{-1} v.
+// partials: 2 * gridDim.x * kMaxDots + gridDim.x doubles.
 __global__ void __launch_bounds__(kRedThreads)
-k_cgs2(int n2, int K, const double *V, double *w, double *partials, double *out, GivensArgs ga, const int *skip) {
+k_cgs2(int n, int K, const double *V, const double *w, double *partials, double *out, GivensArgs ga,
+       const double *Mi, int transpose, double *Vnext, double *z, const int *skip) {
     if (*skip) return;  // uniform over the grid: no block reaches a grid barrier
     cg::grid_group grid = cg::this_grid();
     __shared__ double sh[kRedThreads / 32][kMaxDots];
-    __shared__ double hs[kMaxDots];
+    __shared__ double h1s[kMaxDots], hs[kMaxDots];
+    __shared__ double nrm2_s;
     const int G = gridDim.x;
     const int stride = G * blockDim.x;
-    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double wl[kMaxPer];
+    const size_t n2 = 2 * (size_t)n;
+    double w0[kMaxB], w1[kMaxB];
 #pragma unroll
-    for (int e = 0; e < kMaxPer; ++e) {
-        const int i = i0 + e * stride;
-        wl[e] = i < n2 ? w[i] : 0.0;
+    for (int e = 0; e < kMaxB; ++e) {
+        const int i = b0 + e * stride;
+        w0[e] = i < n ? w[i] : 0.0;
+        w1[e] = i < n ? w[n + i] : 0.0;
     }
     for (int pass = 0; pass < 2; ++pass) {
+        const int nk = pass == 0 ? K : K + 1;  // pass 2 also sums ||w||^2
         double *P = partials + (size_t)pass * G * kMaxDots;
-        for (int k = 0; k < K; ++k) {
-            const double *vk = V + (size_t)k * n2;
+        for (int k = 0; k < nk; ++k) {
             double s = 0.0;
+            if (k < K) {
+                const double *vk = V + (size_t)k * n2;
 #pragma unroll
-            for (int e = 0; e < kMaxPer; ++e) {
-                const int i = i0 + e * stride;
-                if (i < n2) s += vk[i] * wl[e];
+                for (int e = 0; e < kMaxB; ++e) {
+                    const int i = b0 + e * stride;
+                    if (i < n) s += vk[i] * w0[e] + vk[n + i] * w1[e];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kMaxB; ++e) s += w0[e] * w0[e] + w1[e] * w1[e];
             }
             s = warp_sum(s);
             if (lane == 0) sh[warp][k] = s;
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
             double s = 0.0;
             for (int q = 0; q < nw; ++q) s += sh[q][k];
-            P[(size_t)blockIdx.x * K + k] = s;
+            P[(size_t)blockIdx.x * nk + k] = s;
         }
         grid.sync();
-        for (int k = warp; k < K; k += nw) {
+        for (int k = warp; k < nk; k += nw) {
             double s = 0.0;
-            for (int b = lane; b < G; b += 32) s += P[(size_t)b * K + k];
+            for (int b = lane; b < G; b += 32) s += P[(size_t)b * nk + k];
             s = warp_sum(s);
-            if (lane == 0) hs[k] = s;
+            if (lane == 0) {
+                hs[k] = s;
+                if (pass == 0) h1s[k] = s;
+            }
         }
         __syncthreads();
         if (blockIdx.x == 0)
             for (int k = threadIdx.x; k < K; k += blockDim.x) out[pass * kMaxDots + k] = hs[k];
 #pragma unroll
-        for (int e = 0; e < kMaxPer; ++e) {
-            const int i = i0 + e * stride;
-            if (i < n2) {
-                double v = wl[e];
-                for (int k = 0; k < K; ++k) v -= hs[k] * V[(size_t)k * n2 + i];
-                wl[e] = v;
+        for (int e = 0; e < kMaxB; ++e) {
+            const int i = b0 + e * stride;
+            if (i < n) {
+                double v0 = w0[e], v1 = w1[e];
+                for (int k = 0; k < K; ++k) {
+                    v0 -= hs[k] * V[(size_t)k * n2 + i];
+                    v1 -= hs[k] * V[(size_t)k * n2 + n + i];
+                }
+                w0[e] = v0;
+                w1[e] = v1;
             }
         }
         __syncthreads();  // sh and hs are rewritten by the next pass
     }
-    double s = 0.0;
+    if (threadIdx.x == 0) {
+        double t = hs[K];  // ||w||^2 before the second update
+        for (int k = 0; k < K; ++k) t -= hs[k] * hs[k];
+        nrm2_s = t;
+    }
+    __syncthreads();
+    if (!(nrm2_s >= 0.5 * hs[K])) {  // cancellation (or NaN): sum ||w||^2 again
+        double s = 0.0;
 #pragma unroll
-    for (int e = 0; e < kMaxPer; ++e) {
-        const int i = i0 + e * stride;
-        if (i < n2) {
-            w[i] = wl[e];
-            s += wl[e] * wl[e];
+        for (int e = 0; e < kMaxB; ++e) s += w0[e] * w0[e] + w1[e] * w1[e];
+        s = warp_sum(s);
+        __syncthreads();
+        if (lane == 0) sh[warp][0] = s;
+        __syncthreads();
+        double *Pn = partials + (size_t)2 * G * kMaxDots;
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < nw; ++q) t += sh[q][0];
+            Pn[blockIdx.x] = t;
+        }
+        grid.sync();
+        if (warp == 0) {
+            double t = 0.0;
+            for (int b = lane; b < G; b += 32) t += Pn[b];
+            t = warp_sum(t);
+            if (lane == 0) nrm2_s = t;
+        }
+        __syncthreads();
+    }
+    const double nrm2 = nrm2_s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[2 * kMaxDots] = nrm2;
+        givens_column(ga.gm, ga.m, K - 1, h1s, hs, nrm2, ga.beta2, ga.beta_scale, ga.first_cycle, ga.rtol, ga.total,
+                      ga.max_iter, ga.flags, ga.st);
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+#pragma unroll
+    for (int e = 0; e < kMaxB; ++e) {
+        const int i = b0 + e * stride;
+        if (i < n) {
+            const double v0 = inv * w0[e], v1 = inv * w1[e];
+            Vnext[i] = v0;
+            Vnext[n + i] = v1;
+            double z0, z1;
+            minv_apply(Mi, n, i, transpose, v0, v1, z0, z1);
+            z[i] = z0;
+            z[n + i] = z1;
         }
     }
-    s = warp_sum(s);
-    if (lane == 0) sh[warp][0] = s;
+}
+
+// Newton residual of the trapezoid step in one cooperative kernel over
+// bodies: r = x - xprev - hdt (f(x) + fprev), ||r||^2 and ||x||^2 reduced in a
+// fixed order that every block repeats, the Newton test (converged when
+// ||r|| <= tol max(1, ||x||)) taken identically in every block.  Block 0 writes
+// st = {stop, ||r||, ||x||} (stop 0 go on, 1 converged, 2 non-finite, 3 at
+// the iteration limit), flags[0] = stop != 0 and redout[0..1] = the squared
+// norms.  With refresh set the preconditioner blocks M_i^{-1} are first
+// rebuilt from D.  When the iteration goes on, mode 1 applies the
+// block-diagonal Newton update x += M^{-1}(-r); mode 2 writes the first
+// Arnoldi vector v_0 = -r / ||r|| and z = M^{-1} v_0 for GMRES.
+struct NewtonArgs {
+    int n;
+    double *x, *xprev;
+    const double *fxi, *fprev;
+    double hdt;
+    double *r, *partials, *redout;
+    double tol;
+    int limit;
+    int *flags;
+    double *st;
+    int refresh;
+    const double *D;
+    double *Mi;
+    int mode;
+    double *V0, *z;
+    int first;              // k = 0: xprev := x (x^{n-1}) and counter := 0
+    double *f_out;          // f(x) -> f_out when the iteration stops (converged or at the limit)
+    double *d;              // mode 2: d := 0 (the GMRES correction)
+    unsigned int *counter;  // the non-cooperative reductions' arrival counter
+};
+__global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sh[2][kRedThreads / 32];
+    __shared__ double tot[2];
+    const int n = a.n, G = gridDim.x, stride = G * blockDim.x;
+    const int b0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double r0[kMaxB], r1[kMaxB];
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int e = 0; e < kMaxB; ++e) {
+        const int i = b0 + e * stride;
+        r0[e] = 0.0;
+        r1[e] = 0.0;
+        if (i < n) {
+            if (a.refresh) minv_fill(a.D, a.Mi, n, i, a.hdt);
+            const double x0 = a.x[i], x1 = a.x[n + i];
+            double xp0, xp1;
+            if (a.first) {
+                xp0 = x0;
+                xp1 = x1;
+                a.xprev[i] = x0;
+                a.xprev[n + i] = x1;
+            } else {
+                xp0 = a.xprev[i];
+                xp1 = a.xprev[n + i];
+            }
+            const double v0 = x0 - xp0 - a.hdt * (a.fxi[i] + a.fprev[i]);
+            const double v1 = x1 - xp1 - a.hdt * (a.fxi[n + i] + a.fprev[n + i]);
+            a.r[i] = v0;
+            a.r[n + i] = v1;
+            r0[e] = v0;
+            r1[e] = v1;
+            s0 += v0 * v0 + v1 * v1;
+            s1 += x0 * x0 + x1 * x1;
+        }
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if (lane == 0) {
+        sh[0][warp] = s0;
+        sh[1][warp] = s1;
+    }
     __syncthreads();
-    double *Pn = partials + (size_t)2 * G * kMaxDots;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 2) {
         double t = 0.0;
-        for (int q = 0; q < nw; ++q) t += sh[q][0];
-        Pn[blockIdx.x] = t;
+        for (int q = 0; q < nw; ++q) t += sh[threadIdx.x][q];
+        a.partials[(size_t)blockIdx.x * 2 + threadIdx.x] = t;
     }
     grid.sync();
-    if (blockIdx.x == 0 && warp == 0) {
+    if (warp < 2) {
         double t = 0.0;
-        for (int b = lane; b < G; b += 32) t += Pn[b];
+        for (int b = lane; b < G; b += 32) t += a.partials[(size_t)b * 2 + warp];
         t = warp_sum(t);
-        if (lane == 0) {
-            out[2 * kMaxDots] = t;
-            givens_column(ga.gm, ga.m, K - 1, out, out + kMaxDots, t, ga.beta2, ga.beta_scale, ga.first_cycle,
-                          ga.rtol, ga.total, ga.max_iter, ga.flags, ga.st);
+        if (lane == 0) tot[warp] = t;
+    }
+    __syncthreads();
+    const double rn = sqrt(tot[0]), xn = sqrt(tot[1]);
+    const bool conv = rn <= a.tol * (xn > 1.0 ? xn : 1.0);
+    const int stop = !isfinite(rn) ? 2 : (conv ? 1 : (a.limit ? 3 : 0));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.flags[0] = stop != 0;
+        a.st[0] = stop;
+        a.st[1] = rn;
+        a.st[2] = xn;
+        a.redout[0] = tot[0];
+        a.redout[1] = tot[1];
+        if (a.first) *a.counter = 0u;
+    }
+    if (stop == 1 || stop == 3) {  // the step ends here: f(x^n) into f
+#pragma unroll
+        for (int e = 0; e < kMaxB; ++e) {
+            const int i = b0 + e * stride;
+            if (i < n) {
+                a.f_out[i] = a.fxi[i];
+                a.f_out[n + i] = a.fxi[n + i];
+            }
+        }
+    }
+    if (stop != 0 || a.mode == 0) return;
+    const double inv = 1.0 / rn;
+#pragma unroll
+    for (int e = 0; e < kMaxB; ++e) {
+        const int i = b0 + e * stride;
+        if (i >= n) continue;
+        if (a.mode == 1) {
+            double z0, z1;
+            minv_apply(a.Mi, n, i, 0, -r0[e], -r1[e], z0, z1);
+            a.x[i] += z0;
+            a.x[n + i] += z1;
+        } else {
+            const double v0 = inv * -r0[e], v1 = inv * -r1[e];
+            a.V0[i] = v0;
+            a.V0[n + i] = v1;
+            a.d[i] = 0.0;
+            a.d[n + i] = 0.0;
+            double z0, z1;
+            minv_apply(a.Mi, n, i, 0, v0, v1, z0, z1);
+            a.z[i] = z0;
+            a.z[n + i] = z1;
         }
     }
 }
@@ -562,6 +778,7 @@ constexpr int kStatSlots = kMaxRestart + 1;
 struct Work {
     double *xprev, *fprev, *fxi, *r, *D, *d, *jz, *w, *z, *b, *V, *partials, *redout, *M;
     double *stat;  // [kStatSlots][kStatDoubles]
+    double *Mi;    // [4][n] preconditioner blocks (M_i^{-1})
     GmDev gm;
     void *pack;
     unsigned int *counter;
@@ -595,6 +812,7 @@ static Work layout(const ptrom_fom_params *p, int n, char *base) {
     W.fxi = (double *)take(n2 * 8);
     W.r = (double *)take(n2 * 8);
     W.D = (double *)take(3 * (size_t)n * 8);
+    W.Mi = (double *)take(4 * (size_t)n * 8);
     W.d = (double *)take(n2 * 8);
     W.jz = (double *)take(n2 * 8);
     W.w = (double *)take(n2 * 8);
@@ -603,7 +821,7 @@ static Work layout(const ptrom_fom_params *p, int n, char *base) {
     const int m = (p->jac_mode == PTROM_JAC_JFNK) ? p->gmres_restart : 0;
     W.V = (double *)take((size_t)(m + 1) * n2 * 8);
     // reductions: per-block partials, 2 passes of dots + 1 norm (k_cgs2)
-    const int rg = std::max(red_grid((int)n2), 2 * device_sm_count());
+    const int rg = std::max(std::max(red_grid((int)n2), 2 * device_sm_count()), coop_grid(n));
     W.partials = (double *)take(((size_t)2 * rg * kMaxDots + rg) * 8);
     W.redout = (double *)take(4 * kMaxDots * 8);
     W.counter = (unsigned int *)take(64);
@@ -657,21 +875,24 @@ struct Ctx {
     cudaStream_t st;
     Work W;
     int grid, rgrid;
-    bool coop = false;  // CGS2 as one cooperative kernel (rgrid blocks co-resident)
+    int cgrid = 1;      // blocks of the cooperative kernels
+    bool coop = false;  // cooperative CGS2 / Newton kernels (cgrid blocks co-resident)
     ptrom_fom_stats *stats;
     double *mb = nullptr;        // pinned status mailbox [kStatSlots][kStatDoubles]
     cudaEvent_t *ev = nullptr;   // one event per mailbox slot
 };
 
-// Whether `blocks` CTAs of k_cgs2 fit on the device at once.
-static bool cgs2_coop_fits(int blocks) {
+// Whether `blocks` CTAs of the cooperative FOM kernels (k_cgs2, k_newton) fit
+// on the device at once and cover n bodies with kMaxB bodies per thread.
+static bool coop_fits(int blocks, int n) {
     static int per_sm = -1;
     if (per_sm < 0) {
-        int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_cgs2, kRedThreads, 0) != cudaSuccess) v = 0;
-        per_sm = v;
+        int v1 = 0, v2 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v1, k_cgs2, kRedThreads, 0) != cudaSuccess) v1 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v2, k_newton, kRedThreads, 0) != cudaSuccess) v2 = 0;
+        per_sm = v1 < v2 ? v1 : v2;
     }
-    return blocks <= per_sm * device_sm_count();
+    return blocks <= per_sm * device_sm_count() && (long long)blocks * kRedThreads * kMaxB >= n;
 }
 
 static Red mkred(const Work &W, int slot) { return Red{W.partials, W.counter, W.redout + slot * kMaxDots}; }
@@ -746,25 +967,30 @@ static int queue_step(Ctx &c, const Cycle &cy, int j, Slots *slots) {
     const int n2 = c.n2, m = c.p->gmres_restart;
     const int *skip = W.flags;
     double *vj = W.V + (size_t)j * n2;
-    // v_j = previous Krylov vector / its norm (read on the device); z = M^{-1} v_j
-    const double *src = j == 0 ? cy.r0 : W.w;
-    const double *nrm2 = j == 0 ? cy.r0_nrm2 : W.redout + 3 * kMaxDots;
-    const double sc = j == 0 ? cy.r0_scale : 1.0;
-    PTROM_TIMED(PTROM_K_FOM_VEC, c.st, slots,
-                k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, src, sc, nrm2, W.D, c.hdt, c.transpose, vj, W.z, skip));
-    count_launch();
+    // v_j = previous Krylov vector / its norm (read on the device); z = M^{-1} v_j.
+    // The cooperative path has these from the kernel that ended step j - 1
+    // (or from k_newton / the cycle set-up for j = 0).
+    if (!c.coop) {
+        const double *src = j == 0 ? cy.r0 : W.w;
+        const double *nrm2 = j == 0 ? cy.r0_nrm2 : W.redout + 3 * kMaxDots;
+        const double sc = j == 0 ? cy.r0_scale : 1.0;
+        PTROM_TIMED(PTROM_K_FOM_VEC, c.st, slots,
+                    k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, src, sc, nrm2, W.Mi, c.transpose, vj, W.z, skip));
+        count_launch();
+    }
     PTROM_TRY(apply_jvp(c, W.z, W.w, true, skip, slots));  // w = (I - hdt J) z
     GivensArgs ga{W.gm, m, cy.r0_nrm2, cy.r0_scale, cy.first, c.p->gmres_rtol, cy.total + j + 1,
                   c.p->gmres_max_iter, W.flags, W.stat + (1 + j) * kStatDoubles};
     int K = j + 1;
     if (c.coop) {
-        const double *V = W.V;
-        double *w = W.w, *P = W.partials, *out = W.redout + kMaxDots;
-        int n2v = n2;
-        void *args[] = {&n2v, &K, &V, &w, &P, &out, &ga, &skip};
+        const double *V = W.V, *Mi = W.Mi;
+        const double *w = W.w;
+        double *P = W.partials, *out = W.redout + kMaxDots, *Vn = W.V + (size_t)(j + 1) * n2, *z = W.z;
+        int nv = c.n, tr = c.transpose;
+        void *args[] = {&nv, &K, &V, &w, &P, &out, &ga, &Mi, &tr, &Vn, &z, &skip};
         cudaError_t e = cudaSuccess;
         PTROM_TIMED(PTROM_K_FOM_ORTH, c.st, slots,
-                    e = cudaLaunchCooperativeKernel((void *)k_cgs2, dim3(c.rgrid), dim3(kRedThreads), args, 0, c.st));
+                    e = cudaLaunchCooperativeKernel((void *)k_cgs2, dim3(c.cgrid), dim3(kRedThreads), args, 0, c.st));
         PTROM_CUDA(e);
         count_launch();
     } else {
@@ -786,7 +1012,8 @@ static int queue_step(Ctx &c, const Cycle &cy, int j, Slots *slots) {
 // M = blockdiag(I - hdt D_i); d starts at 0.  rhs_nrm2: device ||rhs||^2.
 // With x_upd given, x_upd += d at the end (the Newton update).
 // queued: Arnoldi steps of the first cycle the caller has already queued
-// (0 or 1), with their timing slots in slots[].
+// (0 or 1, with their timing slots in *first); the caller then has also
+// written v_0 and z = M^{-1} v_0 (k_newton).
 //
 // Pipelining: step j + 1 is queued before the host waits for step j's status,
 // so the GPU never waits for the host inside a cycle; when step j stops the
@@ -802,7 +1029,15 @@ static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d, double 
     double bnorm = 0.0;
     while (true) {
         int next = queued;
-        if (next == 0) PTROM_TRY(queue_step(c, cy, next++, &tslot[0]));
+        if (next == 0) {
+            if (c.coop) {  // v_0 and z for the cooperative path
+                PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                            k_norm_precond<<<c.grid, 256, 0, c.st>>>(c.n, cy.r0, cy.r0_scale, cy.r0_nrm2, W.Mi,
+                                                                     c.transpose, W.V, W.z, nullptr));
+                count_launch();
+            }
+            PTROM_TRY(queue_step(c, cy, next++, &tslot[0]));
+        }
         int K = m;
         bool done = false;
         for (int j = 0; j < m; ++j) {
@@ -828,7 +1063,7 @@ static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d, double 
         for (auto &t : tslot) t.n = 0;
         queued = 0;
         PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
-                    k_combine_precond<<<c.grid, 256, 0, c.st>>>(c.n, K, m, W.V, W.gm, W.D, c.hdt, c.transpose, d,
+                    k_combine_precond<<<c.grid, 256, 0, c.st>>>(c.n, K, m, W.V, W.gm, W.Mi, c.transpose, d,
                                                                  done ? x_upd : nullptr));
         count_launch();
         PTROM_CUDA(cudaGetLastError());
@@ -915,16 +1150,20 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
     c.grid = (c.n2 + 255) / 256;
     if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
     c.rgrid = red_grid(c.n2);
-    c.coop = cgs2_coop_fits(c.rgrid);
+    c.cgrid = coop_grid(n);
+    c.coop = coop_fits(c.cgrid, n);
     PTROM_TRY(host_mailbox(kStatSlots * kStatDoubles, kStatSlots, &c.mb, &c.ev));
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;
     memset(c.stats, 0, sizeof(*c.stats));
     Work &W = c.W;
-    PTROM_CUDA(cudaMemsetAsync(W.counter, 0, 64, c.st));
-    PTROM_CUDA(cudaMemsetAsync(W.flags, 0, 64, c.st));
-    PTROM_CUDA(cudaMemcpyAsync(W.xprev, x, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
-    PTROM_CUDA(cudaMemcpyAsync(W.fprev, f, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
+    // f keeps f(x^{n-1}) until the step's last residual, so it serves as fprev;
+    // the cooperative Newton kernel copies x^{n-1} and zeroes the reduction
+    // counter itself at k = 0
+    if (!c.coop) {
+        PTROM_CUDA(cudaMemsetAsync(W.counter, 0, 64, c.st));
+        PTROM_CUDA(cudaMemcpyAsync(W.xprev, x, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
+    }
     bool have_jac = false;
     for (int k = 0; k <= p->max_iter; ++k) {
         const bool refresh = (k % p->p_it == 0) || !have_jac;
@@ -932,19 +1171,39 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
         vo.scratch = W.pack;
         PTROM_TRY(velocity(n, x, n, x, Gamma, p->delta, W.fxi, refresh ? W.D : nullptr, p->prec, c.st, vo));
         c.stats->velocity_evals++;
-        PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
-                    k_residual<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, x, W.xprev, W.fxi, W.fprev, c.hdt, W.r,
-                                                                 mkred(W, 0), p->tol, k == p->max_iter, W.flags,
-                                                                 W.stat));
-        count_launch();
+        const bool jfnk = p->jac_mode == PTROM_JAC_JFNK;
+        if (c.coop) {
+            // residual, norms, Newton test, M^{-1} refresh and (block-diagonal)
+            // the Newton update or (JFNK) v_0 and z in one cooperative launch
+            NewtonArgs na{n, x, W.xprev, W.fxi, f, c.hdt, W.r, W.partials, W.redout, p->tol,
+                          k == p->max_iter, W.flags, W.stat, refresh ? 1 : 0, W.D, W.Mi,
+                          p->jac_mode == PTROM_JAC_BLOCKDIAG ? 1 : (jfnk ? 2 : 0), W.V, W.z,
+                          k == 0 ? 1 : 0, f, W.d, W.counter};
+            void *args[] = {&na};
+            cudaError_t e = cudaSuccess;
+            PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                        e = cudaLaunchCooperativeKernel((void *)k_newton, dim3(c.cgrid), dim3(kRedThreads), args, 0,
+                                                        c.st));
+            PTROM_CUDA(e);
+            count_launch();
+        } else {
+            if (refresh) {
+                k_minv<<<c.grid, 256, 0, c.st>>>(n, W.D, c.hdt, W.Mi);
+                count_launch();
+            }
+            PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                        k_residual<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, x, W.xprev, W.fxi, f, c.hdt, W.r,
+                                                                     mkred(W, 0), p->tol, k == p->max_iter, W.flags,
+                                                                     W.stat));
+            count_launch();
+        }
         PTROM_CUDA(cudaGetLastError());
         PTROM_TRY(post(c, 0));
         // JFNK: queue the first Arnoldi step before reading the Newton test
         // (it skips itself if the test stops the iteration)
         Slots slot0;
-        const bool jfnk = p->jac_mode == PTROM_JAC_JFNK;
         if (jfnk) {
-            PTROM_CUDA(cudaMemsetAsync(W.d, 0, sizeof(double) * c.n2, c.st));
+            if (!c.coop) PTROM_CUDA(cudaMemsetAsync(W.d, 0, sizeof(double) * c.n2, c.st));
             const Cycle cy{W.r, -1.0, W.redout, 1, 0};
             PTROM_TRY(queue_step(c, cy, 0, &slot0));
         }
@@ -957,14 +1216,17 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
         if (stop != 0) {
             discard(slot0);
             if (stop == 2) return set_error(PTROM_ENAN, "fom_step: non-finite residual at iteration %d", k);
-            PTROM_CUDA(cudaMemcpyAsync(f, W.fxi, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
+            if (!c.coop)  // (the cooperative Newton kernel has copied f(x^n) into f)
+                PTROM_CUDA(cudaMemcpyAsync(f, W.fxi, sizeof(double) * c.n2, cudaMemcpyDeviceToDevice, c.st));
             if (stop == 3) return set_error(PTROM_ENOCONV, "fom_step: %d Newton iterations, |r| = %.3e", k, rn);
             return PTROM_OK;
         }
         c.stats->newton_iters++;
         if (p->jac_mode == PTROM_JAC_BLOCKDIAG) {
-            k_blockdiag<<<c.grid, 256, 0, c.st>>>(n, W.D, W.r, c.hdt, -1.0, x, 1, 0);
-            count_launch();
+            if (!c.coop) {  // (the cooperative residual kernel already applied it)
+                k_blockdiag<<<c.grid, 256, 0, c.st>>>(n, W.D, W.r, c.hdt, -1.0, x, 1, 0);
+                count_launch();
+            }
         } else if (jfnk) {
             // solve (I - hdt J) d = -r; x += d (slot 0 of redout holds ||r||^2)
             PTROM_TRY(gmres(c, W.r, -1.0, W.d, x, W.redout, 1, &slot0));
@@ -1034,7 +1296,8 @@ extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *
     c.grid = (c.n2 + 255) / 256;
     if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
     c.rgrid = red_grid(c.n2);
-    c.coop = cgs2_coop_fits(c.rgrid);
+    c.cgrid = coop_grid(n);
+    c.coop = coop_fits(c.cgrid, n);
     PTROM_TRY(host_mailbox(kStatSlots * kStatDoubles, kStatSlots, &c.mb, &c.ev));
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;
@@ -1047,6 +1310,8 @@ extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *
     po.scratch = W.pack;
     PTROM_TRY(velocity(n, x_n, n, x_n, Gamma, q.delta, W.fxi, W.D, q.prec, c.st, po));
     c.stats->velocity_evals++;
+    k_minv<<<c.grid, 256, 0, c.st>>>(n, W.D, c.hdt, W.Mi);
+    count_launch();
     // mu = (I - h J_n)^{-T} lambda  (mu = 0 when lambda = 0)
     PTROM_CUDA(cudaMemsetAsync(W.d, 0, sizeof(double) * c.n2, c.st));
     k_multidot<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, 1, nullptr, lambda, mkred(W, 0));
