@@ -61,6 +61,10 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // After every block has written its nk partials: the last block sums them
 // into red.out (warp w takes k = w, w + nwarps, ...; lanes stride the blocks;
@@ -126,13 +130,14 @@ __global__ void k_residual(int n2, const double *xi, const double *xprev, const 
 // barrier combines the warps.
 constexpr int kMaxPer = 8;
 constexpr int kMaxB = kMaxPer / 2;  // bodies per thread in the cooperative FOM kernels (at most)
-constexpr int kCoopBodies = 2;      // bodies per thread the cooperative grids are sized for
-// Cooperative grid for n bodies: few blocks keep the grid barriers and the
-// per-block partial sums cheap (the vectors are small; latency, not
-// bandwidth, bounds these kernels).
+// Cooperative grid for n bodies: one block per SM at least.  These kernels
+// are bound by FP64 issue (on GB300 one warp-wide FP64 instruction occupies
+// an SM sub-partition's FP64 unit for ~64 cycles), so the work is spread over
+// every SM; more blocks only when kMaxB bodies per thread do not cover n.
 static int coop_grid(int n) {
-    const int g = (n + kRedThreads * kCoopBodies - 1) / (kRedThreads * kCoopBodies);
-    return g < 1 ? 1 : g;
+    const int need = (n + kRedThreads * kMaxB - 1) / (kRedThreads * kMaxB);
+    const int sms = device_sm_count();
+    return need > sms ? need : sms;
 }
 __global__ void k_multidot(int n2, int K, const double *V, const double *w, Red red, const int *skip = nullptr) {
     if (skip && *skip) return;
@@ -208,10 +213,10 @@ __device__ __forceinline__ void minv_fill(const double *D, double *Mi, int n, in
     Mi[2 * (size_t)n + i] = -m10 * inv;
     Mi[3 * (size_t)n + i] = m00 * inv;
 }
-// z = M_i^{-1} r (M_i^{-T} r when transpose is set)
-__device__ __forceinline__ void minv_apply(const double *Mi, int n, int i, int transpose, double r0, double r1,
-                                           double &z0, double &z1) {
-    const double a = Mi[i], b = Mi[n + i], c = Mi[2 * (size_t)n + i], d = Mi[3 * (size_t)n + i];
+// z = M_i^{-1} r (M_i^{-T} r when transpose is set), in arithmetic type A
+template <typename A>
+__device__ __forceinline__ void minv_apply(const double *Mi, int n, int i, int transpose, A r0, A r1, A &z0, A &z1) {
+    const A a = (A)Mi[i], b = (A)Mi[n + i], c = (A)Mi[2 * (size_t)n + i], d = (A)Mi[3 * (size_t)n + i];
     if (transpose) {
         z0 = a * r0 + c * r1;
         z1 = b * r0 + d * r1;
@@ -253,7 +258,7 @@ __global__ void k_norm_precond(int n, const double *src, double scale, const dou
         V_out[i] = v0;
         V_out[n + i] = v1;
         double z0, z1;
-        minv_apply(Mi, n, i, transpose, v0, v1, z0, z1);
+        minv_apply<double>(Mi, n, i, transpose, v0, v1, z0, z1);
         z[i] = z0;
         z[n + i] = z1;
     }
@@ -274,42 +279,55 @@ struct GmDev {
 // norm (scaled by beta_scale^2).  Writes st = {stop, ||w||, |g_{j+1}|,
 // ||b||} with stop 0 = go on, 1 = converged (|g_{j+1}| <= rtol ||b||), at the
 // iteration limit or breakdown (||w|| = 0), 2 = non-finite; flags[0] = stop != 0.
-__device__ void givens_column(GmDev gm, int m, int j, const double *h1, const double *h2, double nrm2,
-                              const double *beta2, double beta_scale, int first_cycle, double rtol, int total,
-                              int max_iter, int *flags, double *st) {
+// The arithmetic is done in type A (FP32 when the Krylov solve is in FP32,
+// see Ctx::krylov32); the state is stored in FP64.
+template <typename A>
+__device__ void givens_column(GmDev gm, int m, int j, const A *h1, const A *h2, A nrm2, const double *beta2,
+                              double beta_scale, int first_cycle, double rtol, int total, int max_iter, int *flags,
+                              double *st) {
     double *H = gm.H;
     if (j == 0) {
-        const double beta = fabs(beta_scale) * sqrt(*beta2);
+        const A beta = (A)fabs(beta_scale) * sqrt((A)*beta2);
         gm.g[0] = beta;
         gm.scal[1] = beta;
         if (first_cycle) gm.scal[0] = beta;
     }
-    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
-    const double hn = sqrt(nrm2);
-    H[(size_t)(j + 1) * m + j] = hn;
+    A col[kMaxRestart + 1];
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    const A hn = sqrt(nrm2);
+    col[j + 1] = hn;
     int stop = 0;
+    A gj1 = 0;
     if (!isfinite(hn)) {
         stop = 2;
     } else {
         for (int i = 0; i < j; ++i) {
-            const double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
-            H[(size_t)i * m + j] = gm.cs[i] * a + gm.sn[i] * b2;
-            H[(size_t)(i + 1) * m + j] = -gm.sn[i] * a + gm.cs[i] * b2;
+            const A ci = (A)gm.cs[i], si = (A)gm.sn[i];
+            const A a = col[i], b2 = col[i + 1];
+            col[i] = ci * a + si * b2;
+            col[i + 1] = -si * a + ci * b2;
         }
-        const double a = H[(size_t)j * m + j], b2 = H[(size_t)(j + 1) * m + j];
-        const double rr = hypot(a, b2);
-        gm.cs[j] = rr > 0 ? a / rr : 1.0;
-        gm.sn[j] = rr > 0 ? b2 / rr : 0.0;
-        H[(size_t)j * m + j] = rr;
-        H[(size_t)(j + 1) * m + j] = 0.0;
-        gm.g[j + 1] = -gm.sn[j] * gm.g[j];
-        gm.g[j] = gm.cs[j] * gm.g[j];
-        if (fabs(gm.g[j + 1]) <= rtol * gm.scal[0] || total >= max_iter || hn == 0.0) stop = 1;
+        const A a = col[j], b2 = col[j + 1];
+        // the entries are O(1) (unit Krylov vectors, I - hdt J near I), so the
+        // plain norm neither overflows nor underflows; one division
+        const A rr = sqrt(a * a + b2 * b2);
+        const A irr = rr > 0 ? (A)1 / rr : (A)0;
+        const A cj = rr > 0 ? a * irr : (A)1, sj = rr > 0 ? b2 * irr : (A)0;
+        gm.cs[j] = cj;
+        gm.sn[j] = sj;
+        col[j] = rr;
+        col[j + 1] = 0;
+        const A gj = (A)gm.g[j];
+        gj1 = -sj * gj;
+        gm.g[j + 1] = gj1;
+        gm.g[j] = cj * gj;
+        if (fabs(gj1) <= (A)rtol * (A)gm.scal[0] || total >= max_iter || hn == 0) stop = 1;
     }
+    for (int i = 0; i <= j + 1; ++i) H[(size_t)i * m + j] = col[i];
     flags[0] = stop != 0;
     st[0] = stop;
     st[1] = hn;
-    st[2] = fabs(gm.g[j + 1]);
+    st[2] = fabs(gj1);
     st[3] = gm.scal[0];
 }
 
@@ -317,18 +335,19 @@ __device__ void givens_column(GmDev gm, int m, int j, const double *h1, const do
 // K x K block of the rotated H; each block solves it, warp 0, in shared
 // memory), then d += M^{-1} (sum_k y_k V_k); with x given, also x += d (the
 // Newton update after the last cycle).
+template <typename A>
 __global__ void k_combine_precond(int n, int K, int m, const double *V, GmDev gm, const double *Mi, int transpose,
                                   double *d, double *x) {
-    __shared__ double y[kMaxRestart];
+    __shared__ A y[kMaxRestart];
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         for (int i = K - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int k = i + 1 + lane; k < K; k += 32) s += gm.H[(size_t)i * m + k] * y[k];
+            A s = 0;
+            for (int k = i + 1 + lane; k < K; k += 32) s += (A)gm.H[(size_t)i * m + k] * y[k];
             s = warp_sum(s);
             if (lane == 0) {
-                const double hii = gm.H[(size_t)i * m + i];
-                y[i] = hii != 0.0 ? (gm.g[i] - s) / hii : 0.0;
+                const A hii = (A)gm.H[(size_t)i * m + i];
+                y[i] = hii != 0 ? ((A)gm.g[i] - s) / hii : (A)0;
             }
             __syncwarp();
         }
@@ -336,13 +355,13 @@ __global__ void k_combine_precond(int n, int K, int m, const double *V, GmDev gm
     __syncthreads();
     const size_t n2 = 2 * (size_t)n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double u0 = 0.0, u1 = 0.0;
+        A u0 = 0, u1 = 0;
         for (int k = 0; k < K; ++k) {
-            u0 += y[k] * V[k * n2 + i];
-            u1 += y[k] * V[k * n2 + n + i];
+            u0 += y[k] * (A)V[k * n2 + i];
+            u1 += y[k] * (A)V[k * n2 + n + i];
         }
-        double z0, z1;
-        minv_apply(Mi, n, i, transpose, u0, u1, z0, z1);
+        A z0, z1;
+        minv_apply<A>(Mi, n, i, transpose, u0, u1, z0, z1);
         const double d0 = d[i] + z0, d1 = d[n + i] + z1;
         d[i] = d0;
         d[n + i] = d1;
@@ -386,54 +405,67 @@ struct GivensArgs {
 // (givens_column).  Finally every block writes the next Arnoldi vector
 // v = w / ||w|| (Vnext) and its preconditioned image z = M^{-1} v.
 // partials: 2 * gridDim.x * kMaxDots + gridDim.x doubles.
+template <typename A>
 __global__ void __launch_bounds__(kRedThreads)
 k_cgs2(int n, int K, const double *V, const double *w, double *partials, double *out, GivensArgs ga,
        const double *Mi, int transpose, double *Vnext, double *z, const int *skip) {
     if (*skip) return;  // uniform over the grid: no block reaches a grid barrier
     cg::grid_group grid = cg::this_grid();
-    __shared__ double sh[kRedThreads / 32][kMaxDots];
-    __shared__ double h1s[kMaxDots], hs[kMaxDots];
-    __shared__ double nrm2_s;
+    __shared__ A sh[kRedThreads / 32][kMaxDots];
+    __shared__ A h1s[kMaxDots], hs[kMaxDots];
+    __shared__ A nrm2_s;
     const int G = gridDim.x;
     const int stride = G * blockDim.x;
     const int b0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const size_t n2 = 2 * (size_t)n;
-    double w0[kMaxB], w1[kMaxB];
+    // bodies b0 + e * stride; `we` = how many of the e slots this warp uses
+    // (a warp-uniform count, so empty slots issue no FP64 instructions: a
+    // predicated-off FP64 instruction still occupies the slow FP64 pipe)
+    const int wbase = blockIdx.x * blockDim.x + warp * 32;
+    int we = 0;
+    while (we < kMaxB && wbase + we * stride < n) ++we;
+    A w0[kMaxB], w1[kMaxB];
 #pragma unroll
     for (int e = 0; e < kMaxB; ++e) {
         const int i = b0 + e * stride;
-        w0[e] = i < n ? w[i] : 0.0;
-        w1[e] = i < n ? w[n + i] : 0.0;
+        w0[e] = (e < we && i < n) ? (A)w[i] : (A)0;
+        w1[e] = (e < we && i < n) ? (A)w[n + i] : (A)0;
     }
     for (int pass = 0; pass < 2; ++pass) {
         const int nk = pass == 0 ? K : K + 1;  // pass 2 also sums ||w||^2
-        double *P = partials + (size_t)pass * G * kMaxDots;
+        A *P = reinterpret_cast<A *>(partials + (size_t)pass * G * kMaxDots);
         for (int k = 0; k < nk; ++k) {
-            double s = 0.0;
-            if (k < K) {
-                const double *vk = V + (size_t)k * n2;
+            A s = 0;
+            if (we > 0) {
+                if (k < K) {
+                    const double *vk = V + (size_t)k * n2;
 #pragma unroll
-                for (int e = 0; e < kMaxB; ++e) {
-                    const int i = b0 + e * stride;
-                    if (i < n) s += vk[i] * w0[e] + vk[n + i] * w1[e];
+                    for (int e = 0; e < kMaxB; ++e) {
+                        if (e >= we) break;
+                        const int i = b0 + e * stride;
+                        if (i < n) s += (A)vk[i] * w0[e] + (A)vk[n + i] * w1[e];
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < kMaxB; ++e) {
+                        if (e >= we) break;
+                        s += w0[e] * w0[e] + w1[e] * w1[e];
+                    }
                 }
-            } else {
-#pragma unroll
-                for (int e = 0; e < kMaxB; ++e) s += w0[e] * w0[e] + w1[e] * w1[e];
+                s = warp_sum(s);
             }
-            s = warp_sum(s);
             if (lane == 0) sh[warp][k] = s;
         }
         __syncthreads();
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-            double s = 0.0;
+            A s = 0;
             for (int q = 0; q < nw; ++q) s += sh[q][k];
             P[(size_t)blockIdx.x * nk + k] = s;
         }
         grid.sync();
         for (int k = warp; k < nk; k += nw) {
-            double s = 0.0;
+            A s = 0;
             for (int b = lane; b < G; b += 32) s += P[(size_t)b * nk + k];
             s = warp_sum(s);
             if (lane == 0) {
@@ -446,12 +478,13 @@ k_cgs2(int n, int K, const double *V, const double *w, double *partials, double 
             for (int k = threadIdx.x; k < K; k += blockDim.x) out[pass * kMaxDots + k] = hs[k];
 #pragma unroll
         for (int e = 0; e < kMaxB; ++e) {
+            if (e >= we) break;
             const int i = b0 + e * stride;
             if (i < n) {
-                double v0 = w0[e], v1 = w1[e];
+                A v0 = w0[e], v1 = w1[e];
                 for (int k = 0; k < K; ++k) {
-                    v0 -= hs[k] * V[(size_t)k * n2 + i];
-                    v1 -= hs[k] * V[(size_t)k * n2 + n + i];
+                    v0 -= hs[k] * (A)V[(size_t)k * n2 + i];
+                    v1 -= hs[k] * (A)V[(size_t)k * n2 + n + i];
                 }
                 w0[e] = v0;
                 w1[e] = v1;
@@ -460,53 +493,64 @@ k_cgs2(int n, int K, const double *V, const double *w, double *partials, double 
         __syncthreads();  // sh and hs are rewritten by the next pass
     }
     if (threadIdx.x == 0) {
-        double t = hs[K];  // ||w||^2 before the second update
+        A t = hs[K];  // ||w||^2 before the second update
         for (int k = 0; k < K; ++k) t -= hs[k] * hs[k];
         nrm2_s = t;
     }
     __syncthreads();
-    if (!(nrm2_s >= 0.5 * hs[K])) {  // cancellation (or NaN): sum ||w||^2 again
-        double s = 0.0;
+    if (!(nrm2_s >= (A)0.5 * hs[K])) {  // cancellation (or NaN): sum ||w||^2 again
+        A s = 0;
+        if (we > 0) {
 #pragma unroll
-        for (int e = 0; e < kMaxB; ++e) s += w0[e] * w0[e] + w1[e] * w1[e];
-        s = warp_sum(s);
+            for (int e = 0; e < kMaxB; ++e) {
+                if (e >= we) break;
+                s += w0[e] * w0[e] + w1[e] * w1[e];
+            }
+            s = warp_sum(s);
+        }
         __syncthreads();
         if (lane == 0) sh[warp][0] = s;
         __syncthreads();
-        double *Pn = partials + (size_t)2 * G * kMaxDots;
+        A *Pn = reinterpret_cast<A *>(partials + (size_t)2 * G * kMaxDots);
         if (threadIdx.x == 0) {
-            double t = 0.0;
+            A t = 0;
             for (int q = 0; q < nw; ++q) t += sh[q][0];
             Pn[blockIdx.x] = t;
         }
         grid.sync();
         if (warp == 0) {
-            double t = 0.0;
+            A t = 0;
             for (int b = lane; b < G; b += 32) t += Pn[b];
             t = warp_sum(t);
             if (lane == 0) nrm2_s = t;
         }
         __syncthreads();
     }
-    const double nrm2 = nrm2_s;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        out[2 * kMaxDots] = nrm2;
-        givens_column(ga.gm, ga.m, K - 1, h1s, hs, nrm2, ga.beta2, ga.beta_scale, ga.first_cycle, ga.rtol, ga.total,
-                      ga.max_iter, ga.flags, ga.st);
-    }
-    const double inv = 1.0 / sqrt(nrm2);
+    const A nrm2 = nrm2_s;
+    __shared__ A inv_s;
+    if (threadIdx.x == 0) inv_s = (A)1 / sqrt(nrm2);  // once per block
+    __syncthreads();
+    const A inv = inv_s;
 #pragma unroll
     for (int e = 0; e < kMaxB; ++e) {
+        if (e >= we) break;
         const int i = b0 + e * stride;
         if (i < n) {
-            const double v0 = inv * w0[e], v1 = inv * w1[e];
+            const A v0 = inv * w0[e], v1 = inv * w1[e];
             Vnext[i] = v0;
             Vnext[n + i] = v1;
-            double z0, z1;
-            minv_apply(Mi, n, i, transpose, v0, v1, z0, z1);
+            A z0, z1;
+            minv_apply<A>(Mi, n, i, transpose, v0, v1, z0, z1);
             z[i] = z0;
             z[n + i] = z1;
         }
+    }
+    // block 0, one thread: the column into the least squares (after its own
+    // share of the vector writes, which the other blocks do meanwhile)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[2 * kMaxDots] = nrm2;
+        givens_column<A>(ga.gm, ga.m, K - 1, h1s, hs, nrm2, ga.beta2, ga.beta_scale, ga.first_cycle, ga.rtol, ga.total,
+                      ga.max_iter, ga.flags, ga.st);
     }
 }
 
@@ -547,6 +591,9 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
     const int n = a.n, G = gridDim.x, stride = G * blockDim.x;
     const int b0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int wbase = blockIdx.x * blockDim.x + warp * 32;  // warp-uniform body slots, as in k_cgs2
+    int we = 0;
+    while (we < kMaxB && wbase + we * stride < n) ++we;
     double r0[kMaxB], r1[kMaxB];
     double s0 = 0.0, s1 = 0.0;
 #pragma unroll
@@ -554,7 +601,7 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
         const int i = b0 + e * stride;
         r0[e] = 0.0;
         r1[e] = 0.0;
-        if (i < n) {
+        if (e < we && i < n) {
             if (a.refresh) minv_fill(a.D, a.Mi, n, i, a.hdt);
             const double x0 = a.x[i], x1 = a.x[n + i];
             double xp0, xp1;
@@ -577,8 +624,10 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
             s1 += x0 * x0 + x1 * x1;
         }
     }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
+    if (we > 0) {
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+    }
     if (lane == 0) {
         sh[0][warp] = s0;
         sh[1][warp] = s1;
@@ -597,9 +646,20 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
         if (lane == 0) tot[warp] = t;
     }
     __syncthreads();
-    const double rn = sqrt(tot[0]), xn = sqrt(tot[1]);
-    const bool conv = rn <= a.tol * (xn > 1.0 ? xn : 1.0);
-    const int stop = !isfinite(rn) ? 2 : (conv ? 1 : (a.limit ? 3 : 0));
+    // the Newton test once per block (identical in every block), broadcast
+    __shared__ int stop_s;
+    __shared__ double rn_s, xn_s, inv_s;
+    if (threadIdx.x == 0) {
+        const double rn = sqrt(tot[0]), xn = sqrt(tot[1]);
+        const bool conv = rn <= a.tol * (xn > 1.0 ? xn : 1.0);
+        stop_s = !isfinite(rn) ? 2 : (conv ? 1 : (a.limit ? 3 : 0));
+        rn_s = rn;
+        xn_s = xn;
+        inv_s = 1.0 / rn;
+    }
+    __syncthreads();
+    const int stop = stop_s;
+    const double rn = rn_s, xn = xn_s;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.flags[0] = stop != 0;
         a.st[0] = stop;
@@ -613,18 +673,18 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
 #pragma unroll
         for (int e = 0; e < kMaxB; ++e) {
             const int i = b0 + e * stride;
-            if (i < n) {
+            if (e < we && i < n) {
                 a.f_out[i] = a.fxi[i];
                 a.f_out[n + i] = a.fxi[n + i];
             }
         }
     }
     if (stop != 0 || a.mode == 0) return;
-    const double inv = 1.0 / rn;
+    const double inv = inv_s;
 #pragma unroll
     for (int e = 0; e < kMaxB; ++e) {
         const int i = b0 + e * stride;
-        if (i >= n) continue;
+        if (e >= we || i >= n) continue;
         if (a.mode == 1) {
             double z0, z1;
             minv_apply(a.Mi, n, i, 0, -r0[e], -r1[e], z0, z1);
@@ -648,7 +708,7 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
 // to be co-resident): one thread.
 __global__ void k_givens(int K, const double *out, GivensArgs ga, const int *skip) {
     if (*skip) return;
-    givens_column(ga.gm, ga.m, K - 1, out, out + kMaxDots, out[2 * kMaxDots], ga.beta2, ga.beta_scale,
+    givens_column<double>(ga.gm, ga.m, K - 1, out, out + kMaxDots, out[2 * kMaxDots], ga.beta2, ga.beta_scale,
                   ga.first_cycle, ga.rtol, ga.total, ga.max_iter, ga.flags, ga.st);
 }
 
@@ -877,6 +937,12 @@ struct Ctx {
     int grid, rgrid;
     int cgrid = 1;      // blocks of the cooperative kernels
     bool coop = false;  // cooperative CGS2 / Newton kernels (cgrid blocks co-resident)
+    // Krylov arithmetic (CGS2, least squares, correction) in FP32: when the
+    // pair sums are FP32 and the GMRES tolerance is loose (>= 1e-5) the solve
+    // needs no FP64, and on GB300 every dependent FP64 operation costs
+    // hundreds of cycles (the reductions and the scalar chain of one Arnoldi
+    // step are latency-bound).  Vectors stay FP64 in memory either way.
+    bool krylov32 = false;
     ptrom_fom_stats *stats;
     double *mb = nullptr;        // pinned status mailbox [kStatSlots][kStatDoubles]
     cudaEvent_t *ev = nullptr;   // one event per mailbox slot
@@ -888,7 +954,10 @@ static bool coop_fits(int blocks, int n) {
     static int per_sm = -1;
     if (per_sm < 0) {
         int v1 = 0, v2 = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v1, k_cgs2, kRedThreads, 0) != cudaSuccess) v1 = 0;
+        int v3 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v1, k_cgs2<double>, kRedThreads, 0) != cudaSuccess) v1 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v3, k_cgs2<float>, kRedThreads, 0) != cudaSuccess) v3 = 0;
+        v1 = v1 < v3 ? v1 : v3;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v2, k_newton, kRedThreads, 0) != cudaSuccess) v2 = 0;
         per_sm = v1 < v2 ? v1 : v2;
     }
@@ -990,7 +1059,8 @@ static int queue_step(Ctx &c, const Cycle &cy, int j, Slots *slots) {
         void *args[] = {&nv, &K, &V, &w, &P, &out, &ga, &Mi, &tr, &Vn, &z, &skip};
         cudaError_t e = cudaSuccess;
         PTROM_TIMED(PTROM_K_FOM_ORTH, c.st, slots,
-                    e = cudaLaunchCooperativeKernel((void *)k_cgs2, dim3(c.cgrid), dim3(kRedThreads), args, 0, c.st));
+                    e = cudaLaunchCooperativeKernel(c.krylov32 ? (void *)k_cgs2<float> : (void *)k_cgs2<double>,
+                                                    dim3(c.cgrid), dim3(kRedThreads), args, 0, c.st));
         PTROM_CUDA(e);
         count_launch();
     } else {
@@ -1062,9 +1132,15 @@ static int gmres(Ctx &c, const double *rhs, double rhs_scale, double *d, double 
         for (int j = K; j < next; ++j) discard(tslot[j]);  // queued steps that did nothing
         for (auto &t : tslot) t.n = 0;
         queued = 0;
-        PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
-                    k_combine_precond<<<c.grid, 256, 0, c.st>>>(c.n, K, m, W.V, W.gm, W.Mi, c.transpose, d,
-                                                                 done ? x_upd : nullptr));
+        double *xu = done ? x_upd : nullptr;
+        if (c.krylov32)
+            PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                        k_combine_precond<float><<<c.grid, 256, 0, c.st>>>(c.n, K, m, W.V, W.gm, W.Mi, c.transpose,
+                                                                           d, xu));
+        else
+            PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
+                        k_combine_precond<double><<<c.grid, 256, 0, c.st>>>(c.n, K, m, W.V, W.gm, W.Mi, c.transpose,
+                                                                            d, xu));
         count_launch();
         PTROM_CUDA(cudaGetLastError());
         if (done) break;
@@ -1152,6 +1228,7 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
     c.rgrid = red_grid(c.n2);
     c.cgrid = coop_grid(n);
     c.coop = coop_fits(c.cgrid, n);
+    c.krylov32 = c.coop && p->prec == PTROM_FP32C && p->gmres_rtol >= 1e-5;
     PTROM_TRY(host_mailbox(kStatSlots * kStatDoubles, kStatSlots, &c.mb, &c.ev));
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;

@@ -169,3 +169,19 @@ def test_jfnk_iteration_cap_and_counts(P):
     assert st["newton_iters"] >= 1 and st["linear_iters"] >= st["newton_iters"]
     assert t["jvp"][1] == st["jvp_evals"]
     assert t["velocity"][1] + t["velocity_selfjac"][1] == st["velocity_evals"]
+
+
+def test_fp32_krylov_matches_fp64_krylov(P):
+    """With FP32 pair sums and a loose GMRES tolerance (1e-4) the Krylov
+    arithmetic runs in FP32; a tighter tolerance (1e-6) keeps it in FP64.
+    Both Newton iterations stop at the same FP64 residual test
+    (||r|| <= 1e-8 max(1, ||x||)), so the trajectories agree to that level."""
+    x0, G = W.two_cluster(2048, seed=0)
+    p32 = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c", gmres_rtol=1e-4)
+    p64 = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c", gmres_rtol=1e-6)
+    ta, sa, _ = _gpu_rollout(P, x0, G, p32, 5, "fp32c")
+    tb, sb, _ = _gpu_rollout(P, x0, G, p64, 5, "fp32c")
+    xnorm = np.linalg.norm(x0)
+    assert all(s["converged"] and s["res_norm"] <= 1e-8 * xnorm for s in sa + sb)
+    # each end state is within a Newton-tolerance-sized ball of the other
+    assert np.linalg.norm(ta[-1] - tb[-1]) <= 1e-6 * xnorm
