@@ -38,16 +38,9 @@ namespace cg = cooperative_groups;
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kChunk = 32;
-#ifndef PTROM_TGT_SETS
-#define PTROM_TGT_SETS 1
-#endif
-constexpr int kSets = PTROM_TGT_SETS;  // target pairs per lane (independent FP32x2 sets)
-constexpr int kTB = 64 * kSets;        // targets per CTA
+constexpr int kTB = 64;
 constexpr int kMaxCluster = 8;
-#ifndef PTROM_AUTO_SPLIT
-#define PTROM_AUTO_SPLIT 4
-#endif
-constexpr int kAutoSplit = PTROM_AUTO_SPLIT;  // default source split (cluster size)
+constexpr int kAutoSplit = 4;  // default source split (cluster size)
 #ifndef PTROM_PAIR_UNROLL
 #define PTROM_PAIR_UNROLL 8
 #endif
@@ -154,15 +147,12 @@ __device__ __forceinline__ void pair_block(const typename Op::Args &args, const 
     const int warp = threadIdx.x >> 5;
 
     const typename Op::Origin org = Op::origin(args);
-    typename Op::Tgt tgt[kSets];
-#pragma unroll
-    for (int s = 0; s < kSets; ++s) Op::load_tgt(args, tbase + 64 * s + lane, tbase + 64 * s + 32 + lane, org, tgt[s]);
+    typename Op::Tgt tgt;
+    Op::load_tgt(args, tbase + lane, tbase + 32 + lane, org, tgt);
 
-    Acc<R> acc[kSets][NACC];
+    Acc<R> acc[NACC];
 #pragma unroll
-    for (int s = 0; s < kSets; ++s)
-#pragma unroll
-        for (int k = 0; k < NACC; ++k) acc[s][k].zero();
+    for (int k = 0; k < NACC; ++k) acc[k].zero();
 
     const int c_begin = (int)(((long long)blockIdx.y * nchunks) / gridDim.y);
     const int c_end = (int)(((long long)(blockIdx.y + 1) * nchunks) / gridDim.y);
@@ -176,31 +166,23 @@ __device__ __forceinline__ void pair_block(const typename Op::Args &args, const 
         __syncwarp();
         const int cn = c + kWarps;
         if (cn < c_end) reg = packed[cn * kChunk + lane];
-        V part[kSets][NACC];
+        V part[NACC];
 #pragma unroll
-        for (int s = 0; s < kSets; ++s)
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) part[s][k] = VT<R>::mk(0, 0);
+        for (int k = 0; k < NACC; ++k) part[k] = VT<R>::mk(0, 0);
 #pragma unroll kPairUnroll
-        for (int k = 0; k < kChunk; ++k)
+        for (int k = 0; k < kChunk; ++k) Op::pair(stage[warp][b].r[k], tgt, part);
 #pragma unroll
-            for (int s = 0; s < kSets; ++s) Op::pair(stage[warp][b].r[k], tgt[s], part[s]);
-#pragma unroll
-        for (int s = 0; s < kSets; ++s)
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) acc[s][k].add(part[s][k]);
+        for (int k = 0; k < NACC; ++k) acc[k].add(part[k]);
         b ^= 1;
     }
 
     // reduce the 8 warps (fixed order); the staging storage is reused
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < kSets; ++s)
-#pragma unroll
-        for (int k = 0; k < NACC; ++k) {
-            red[warp][k][64 * s + lane] = acc[s][k].x();
-            red[warp][k][64 * s + 32 + lane] = acc[s][k].y();
-        }
+    for (int k = 0; k < NACC; ++k) {
+        red[warp][k][lane] = acc[k].x();
+        red[warp][k][32 + lane] = acc[k].y();
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < NACC * kTB; e += kThreads) {
         const int k = e / kTB, t = e % kTB;
