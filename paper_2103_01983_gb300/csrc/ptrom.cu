@@ -138,7 +138,7 @@ __device__ void hyperpair_residual(const DevModel &m, const float *xhf, const fl
             const int c = __ldg(m.idx + e);
             const float a = tx - xq[c], b = ty - xq[m.Nc + c];
             const float d2 = fmaf(a, a, b * b);
-            float rr = 1.0f / (d2 + dd);
+            float rr = rcp_approx(d2 + dd);  // MUFU reciprocal, ~1 ulp (as in the all-pairs kernels)
             rr = (d2 == 0.f) ? 0.f : rr;
             const float q = gq[c] * rr;
             u = fmaf(q, b, u);
