@@ -41,12 +41,16 @@ struct DevStats {
 
 // ------------------------------------------------------------------ layout
 struct SmemLayout {
-    size_t xh, xp, dx, xhf, df, red, f, fp, r, D, xq, gq, Bf, Bd, Ct, Ats, total;
+    size_t xh, xp, dx, xhf, df, red, f, fp, r, D, xq, gq, Bf, Bd, Ct, Ats, phiS, At, idx, total;
 };
 
 __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__host__ __device__ inline SmemLayout smem_layout(int ns, int M, int Mr, int Nc, int Mp, int Mrp, int qr64) {
+// rows / idx: also reserve the staged Phi_s and A^T rows / the 16-bit cluster
+// lists (nlist entries), constant for the whole launch and read every
+// Gauss-Newton iteration.
+__host__ __device__ inline SmemLayout smem_layout(int ns, int M, int Mr, int Nc, int Mp, int Mrp, int qr64,
+                                                  int rows = 0, int idx = 0, int nlist = 0) {
     SmemLayout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o += al16(bytes); return at; };
@@ -66,6 +70,9 @@ __host__ __device__ inline SmemLayout smem_layout(int ns, int M, int Mr, int Nc,
     L.Bd = take(qr64 ? 8 * (size_t)Mrp * (M + 1) : 0);
     L.Ct = take(4 * 2 * kTileB * (size_t)Mp);
     L.Ats = take(4 * 2 * kTileB * (size_t)Mrp);
+    L.phiS = take(rows ? 4 * 2 * (size_t)ns * Mp : 0);
+    L.At = take(rows ? 4 * 2 * (size_t)ns * Mrp : 0);
+    L.idx = take(idx ? 2 * (size_t)nlist : 0);
     L.total = o;
     return L;
 }
@@ -97,18 +104,28 @@ __device__ void gather_clusters(const DevModel &m, const double *xh, const doubl
         df[k] = k < m.M ? (float)(xh[k] - xp[k]) : 0.f;
     }
     __syncthreads();
-    for (int row = threadIdx.x; row < 2 * m.Nc; row += kPT) {
-        const float *ph = m.phiT + (size_t)row * m.Mp;
-        float acc = m.x0T[row];
+    // two rows per thread per round, so twice the L2 loads are in flight
+    const int rows = 2 * m.Nc;
+    for (int row = threadIdx.x; row < rows; row += 2 * kPT) {
+        const int row2 = row + kPT;
+        const bool two = row2 < rows;
+        const float *ph = m.phiT + (size_t)row * m.Mp, *ph2 = m.phiT + (size_t)(two ? row2 : row) * m.Mp;
+        float acc = m.x0T[row], acc2 = two ? m.x0T[row2] : 0.f;
 #pragma unroll 4
         for (int k = 0; k < m.Mp; k += 4) {
             const float4 p = __ldg(reinterpret_cast<const float4 *>(ph + k));
+            const float4 p2 = __ldg(reinterpret_cast<const float4 *>(ph2 + k));
             acc = fmaf(p.x, xhf[k], acc);
             acc = fmaf(p.y, xhf[k + 1], acc);
             acc = fmaf(p.z, xhf[k + 2], acc);
             acc = fmaf(p.w, xhf[k + 3], acc);
+            acc2 = fmaf(p2.x, xhf[k], acc2);
+            acc2 = fmaf(p2.y, xhf[k + 1], acc2);
+            acc2 = fmaf(p2.z, xhf[k + 2], acc2);
+            acc2 = fmaf(p2.w, xhf[k + 3], acc2);
         }
         xq[row] = acc;
+        if (two) xq[row2] = acc2;
     }
     __syncthreads();
 }
@@ -116,18 +133,21 @@ __device__ void gather_clusters(const DevModel &m, const double *xh, const doubl
 // dot of a Phi_s row with a shared-memory vector, lanes over the modes.
 __device__ __forceinline__ float row_dot(const float *row, const float *vec, int Mp, int lane) {
     float s = 0.f;
-    for (int k = lane; k < Mp; k += 32) s = fmaf(__ldg(row + k), vec[k], s);
+    for (int k = lane; k < Mp; k += 32) s = fmaf(row[k], vec[k], s);
     return warp_allsum(s);
 }
 
 // Phase B, warp per sampled body i: x~_i, the HyperPair sums f~_i and D~_i
 // over its clusters, and the residual r_i = Phi_s,i dxhat - h (f~_i + f~^{n-1}_i).
-__device__ void hyperpair_residual(const DevModel &m, const float *xhf, const float *df, const float *xq,
-                                   const float *gq, const float *fp, float *f, float *D, float *r) {
+// phiB: the Phi_s rows (shared or global memory); idx16: the cluster lists in
+// shared memory as 16-bit indices, or nullptr to read m.idx.
+__device__ void hyperpair_residual(const DevModel &m, const float *phiB, const unsigned short *idx16,
+                                   const float *xhf, const float *df, const float *xq, const float *gq,
+                                   const float *fp, float *f, float *D, float *r) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float dd = (float)m.delta, h = (float)(0.5 * m.dt);
     for (int i = warp; i < m.ns; i += kPT / 32) {
-        const float *rc = m.phiB + (size_t)i * m.Mp, *rp = m.phiB + (size_t)(m.ns + i) * m.Mp;
+        const float *rc = phiB + (size_t)i * m.Mp, *rp = phiB + (size_t)(m.ns + i) * m.Mp;
         const float tx = m.x0B[i] + row_dot(rc, xhf, m.Mp, lane);
         const float ty = m.x0B[m.ns + i] + row_dot(rp, xhf, m.Mp, lane);
         const float gx = row_dot(rc, df, m.Mp, lane), gy = row_dot(rp, df, m.Mp, lane);
@@ -135,7 +155,7 @@ __device__ void hyperpair_residual(const DevModel &m, const float *xhf, const fl
         const int e_end = m.off[i + 1];
 #pragma unroll 4
         for (int e = m.off[i] + lane; e < e_end; e += 32) {
-            const int c = __ldg(m.idx + e);
+            const int c = idx16 ? (int)idx16[e] : __ldg(m.idx + e);
             const float a = tx - xq[c], b = ty - xq[m.Nc + c];
             const float d2 = fmaf(a, a, b * b);
             float rr = rcp_approx(d2 + dd);  // MUFU reciprocal, ~1 ulp (as in the all-pairs kernels)
@@ -170,8 +190,9 @@ __device__ void hyperpair_residual(const DevModel &m, const float *xhf, const fl
 // Phase C: B[:, 0..M-1] = A C (C = J Phi_s), B[:, M] = A r; B column-major
 // (ld Mrp), FP32.  Each tile of 16 bodies (32 dofs) stages its rows of A^T
 // and of C in shared memory with one cooperative round of loads.
-__device__ void assemble_lsq(const DevModel &m, const float *D, const float *r, float *Ct, float *Ats,
-                             float *B) {
+// phiB, At: the Phi_s and A^T rows (shared or global memory).
+__device__ void assemble_lsq(const DevModel &m, const float *phiB, const float *At, const float *D, const float *r,
+                             float *Ct, float *Ats, float *B) {
     const float h = (float)(0.5 * m.dt);
     const int tilesM = m.Mp / 4, tilesR = m.Mrp / 4;
     const int t = threadIdx.x;
@@ -187,7 +208,7 @@ __device__ void assemble_lsq(const DevModel &m, const float *D, const float *r, 
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (j < nbt) {
                 const int dof = (slot & 1) ? m.ns + i0 + j : i0 + j;
-                v = __ldg(reinterpret_cast<const float4 *>(m.At + (size_t)dof * m.Mrp) + c4);
+                v = reinterpret_cast<const float4 *>(At + (size_t)dof * m.Mrp)[c4];
             }
             reinterpret_cast<float4 *>(Ats + (size_t)slot * m.Mrp)[c4] = v;
         }
@@ -197,7 +218,7 @@ __device__ void assemble_lsq(const DevModel &m, const float *D, const float *r, 
             float val = 0.f;
             if (j < nbt) {
                 const int i = i0 + j;
-                const float pc = __ldg(m.phiB + (size_t)i * m.Mp + k), pp = __ldg(m.phiB + (size_t)(m.ns + i) * m.Mp + k);
+                const float pc = phiB[(size_t)i * m.Mp + k], pp = phiB[(size_t)(m.ns + i) * m.Mp + k];
                 const float d00 = D[i], d01 = D[m.ns + i], d10 = D[2 * m.ns + i];
                 val = (slot & 1) ? pp - h * (d10 * pc - d00 * pp) : pc - h * (d00 * pc + d01 * pp);
             }
@@ -253,57 +274,91 @@ __device__ float lsq_gradient(const DevModel &m, const float *B, float *red) {
 }
 
 // Householder QR of B (Mr x M, column-major, rhs in column M) in T arithmetic,
-// then dx = -R^{-1} (Q^T b)[0..M-1].  Two CTA barriers per column.
+// then dx = -R^{-1} (Q^T b)[0..M-1].  Every warp computes column j's
+// Householder vector itself from the same data (identical in all warps), so
+// one CTA barrier per column suffices: warps then update the later columns
+// k = j+1+warp, j+1+warp+16, ... in parallel.
+template <typename T>
+__device__ __forceinline__ T warp_allsum_t(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sqrt and reciprocal: exact in FP64; MUFU (~1 ulp) in FP32, since the FP32
+// solve's IEEE sequences sit on a chain of 20 dependent steps per column loop
+// and the Gauss-Newton fixed point is set by the residual, not by the solve
+__device__ __forceinline__ double ls_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ double ls_rcp(double v) { return 1.0 / v; }
+__device__ __forceinline__ float ls_sqrt(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
+__device__ __forceinline__ float ls_rcp(float v) { return rcp_approx(v); }
+
 template <typename T>
 __device__ void lsq_solve(const DevModel &m, T *B, double *dx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Mr = m.Mr, M = m.M, ld = m.Mrp;
-    __shared__ T s_alpha[kMaxM], s_tau;
+    __shared__ T s_alpha[kMaxM], s_y[kMaxM], s_rem[kMaxM], s_ref[kMaxM];
     const int ncols = min(M, Mr);
+    // remaining squared norm of every column over the rows not yet reduced
+    // (downdated after each reflection: |c_k[j..]|^2 = |c_k[j-1..]|^2 - R_{j-1,k}^2,
+    // as in QR with column pivoting), so a column's reflector needs no reduction
+    for (int k = warp; k < ncols; k += kPT / 32) {
+        const T *ck = B + (size_t)k * ld;
+        T s = 0;
+        for (int i = lane; i < Mr; i += 32) s += ck[i] * ck[i];
+        s = warp_allsum_t(s);
+        if (lane == 0) s_rem[k] = s_ref[k] = s;
+    }
+    __syncthreads();
     for (int j = 0; j < ncols; ++j) {
-        T *cj = B + (size_t)j * ld;
-        if (warp == 0) {
-            T s = 0;
+        const T *cj = B + (size_t)j * ld;
+        T s = s_rem[j];
+        // each downdate errs by ~eps |c_j|^2 <= eps s_ref: while half of the
+        // norm remains the value is good to ~40 eps; otherwise sum it again
+        // (the same branch in every warp: the values are shared)
+        if (!(s >= (T)0.5 * s_ref[j])) {
+            s = 0;
             for (int i = j + lane; i < Mr; i += 32) s += cj[i] * cj[i];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                const T x0 = cj[j];
-                const T nrm = sqrt(s);
-                const T alpha = x0 >= 0 ? -nrm : nrm;
-                const T v0 = x0 - alpha;
-                const T vn2 = s - x0 * x0 + v0 * v0;
-                s_alpha[j] = alpha;
-                s_tau = vn2 > 0 ? (T)2 / vn2 : (T)0;
-                cj[j] = v0;  // v = (v0, cj[j+1..])
-            }
+            s = warp_allsum_t(s);
         }
-        __syncthreads();
-        const T tau = s_tau;
+        const T x0 = cj[j];
+        const T nrm = ls_sqrt(s);
+        const T alpha = x0 >= 0 ? -nrm : nrm;
+        const T v0 = x0 - alpha;  // v = (v0, cj[j+1..])
+        const T vn2 = s - x0 * x0 + v0 * v0;
+        const T tau = vn2 > 0 ? (T)2 * ls_rcp(vn2) : (T)0;
+        if (threadIdx.x == 0) s_alpha[j] = alpha;
         for (int k = j + 1 + warp; k <= M; k += kPT / 32) {
             T *ck = B + (size_t)k * ld;
             T w = 0;
-            for (int i = j + lane; i < Mr; i += 32) w += cj[i] * ck[i];
-            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-            w *= tau;
-            for (int i = j + lane; i < Mr; i += 32) ck[i] -= w * cj[i];
+            for (int i = j + lane; i < Mr; i += 32) w += (i == j ? v0 : cj[i]) * ck[i];
+            w = warp_allsum_t(w) * tau;
+            for (int i = j + lane; i < Mr; i += 32) {
+                const T c = ck[i] - w * (i == j ? v0 : cj[i]);
+                ck[i] = c;
+                if (i == j && k < ncols) s_rem[k] -= c * c;  // row j of column k is now R_jk
+            }
         }
-        __syncthreads();
+        __syncthreads();  // the updated columns (and remaining norms) are read by every warp next
     }
-    // back substitution R dx = -c (warp 0); R's diagonal is s_alpha
+    // back substitution R y = -c (warp 0, in T), column by column: lane l
+    // holds the right-hand sides of rows l and l + 32; each step broadcasts
+    // y_j from its row's lane and updates the rows above it (R_ij is column
+    // j's row i; R's diagonal is s_alpha), one shuffle and one FMA per step
     if (warp == 0) {
         const T *rhs = B + (size_t)M * ld;
+        T c0 = lane < ncols ? -rhs[lane] : (T)0, c1 = lane + 32 < ncols ? -rhs[lane + 32] : (T)0;
         for (int j = ncols - 1; j >= 0; --j) {
-            T s = 0;
-            for (int k = j + 1 + lane; k < ncols; k += 32) s += B[(size_t)k * ld + j] * (T)dx[k];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                const T rjj = s_alpha[j];
-                dx[j] = rjj != 0 ? (double)((-rhs[j] - s) / rjj) : 0.0;
-            }
-            __syncwarp();
+            const T cj = j < 32 ? __shfl_sync(0xffffffffu, c0, j) : __shfl_sync(0xffffffffu, c1, j - 32);
+            const T rjj = s_alpha[j];
+            const T yj = rjj != 0 ? cj * ls_rcp(rjj) : (T)0;
+            if (lane == (j & 31)) s_y[j] = yj;
+            const T *cjc = B + (size_t)j * ld;
+            if (lane < j) c0 -= cjc[lane] * yj;
+            if (lane + 32 < j) c1 -= cjc[lane + 32] * yj;
         }
-        for (int j = ncols + lane; j < M; j += 32) dx[j] = 0.0;
     }
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += kPT) dx[j] = j < ncols ? (double)s_y[j] : 0.0;
     __syncthreads();
 }
 
@@ -312,7 +367,7 @@ k_ptrom(const InstArgs *__restrict__ insts, int nsteps, DevStats *stats) {
     extern __shared__ __align__(16) unsigned char sm[];
     const InstArgs &I = insts[blockIdx.x];
     const DevModel m = I.m;
-    const SmemLayout L = smem_layout(m.ns, m.M, m.Mr, m.Nc, m.Mp, m.Mrp, m.qr64);
+    const SmemLayout L = smem_layout(m.ns, m.M, m.Mr, m.Nc, m.Mp, m.Mrp, m.qr64, m.cache_rows, m.cache_idx, m.nlist);
     double *xh = (double *)(sm + L.xh), *xp = (double *)(sm + L.xp), *dx = (double *)(sm + L.dx);
     float *xhf = (float *)(sm + L.xhf), *df = (float *)(sm + L.df), *red = (float *)(sm + L.red);
     float *f = (float *)(sm + L.f), *fp = (float *)(sm + L.fp), *r = (float *)(sm + L.r), *D = (float *)(sm + L.D);
@@ -326,12 +381,27 @@ k_ptrom(const InstArgs *__restrict__ insts, int nsteps, DevStats *stats) {
         xp[k] = st_x[k];
     }
     for (int c = threadIdx.x; c < m.Nc; c += kPT) gq[c] = m.gT[c];
+    // constant model rows and lists, read every Gauss-Newton iteration: staged once
+    const float *phiB = m.phiB, *At = m.At;
+    const unsigned short *idx16 = nullptr;
+    if (m.cache_rows) {
+        float *ps = (float *)(sm + L.phiS), *as = (float *)(sm + L.At);
+        for (int e = threadIdx.x; e < 2 * m.ns * m.Mp; e += kPT) ps[e] = m.phiB[e];
+        for (int e = threadIdx.x; e < 2 * m.ns * m.Mrp; e += kPT) as[e] = m.At[e];
+        phiB = ps;
+        At = as;
+    }
+    if (m.cache_idx) {
+        unsigned short *is = (unsigned short *)(sm + L.idx);
+        for (int e = threadIdx.x; e < m.nlist; e += kPT) is[e] = (unsigned short)m.idx[e];
+        idx16 = is;
+    }
     const bool have_f = st_flag[0] != 0.0;
     for (int d = threadIdx.x; d < 2 * m.ns; d += kPT) fp[d] = have_f ? (float)st_f[d] : 0.f;
     __syncthreads();
     if (!have_f) {  // f~ at the initial coordinates (R11)
         gather_clusters(m, xh, xp, xhf, df, xq);
-        hyperpair_residual(m, xhf, df, xq, gq, fp, f, D, r);
+        hyperpair_residual(m, phiB, idx16, xhf, df, xq, gq, fp, f, D, r);
         for (int d = threadIdx.x; d < 2 * m.ns; d += kPT) fp[d] = f[d];
         __syncthreads();
     }
@@ -343,8 +413,8 @@ k_ptrom(const InstArgs *__restrict__ insts, int nsteps, DevStats *stats) {
         int kk = 0;
         while (true) {
             gather_clusters(m, xh, xp, xhf, df, xq);
-            hyperpair_residual(m, xhf, df, xq, gq, fp, f, D, r);
-            assemble_lsq(m, D, r, Ct, Ats, Bf);
+            hyperpair_residual(m, phiB, idx16, xhf, df, xq, gq, fp, f, D, r);
+            assemble_lsq(m, phiB, At, D, r, Ct, Ats, Bf);
             const float g = lsq_gradient(m, Bf, red);
             if (m.qr64) {
                 for (int e = threadIdx.x; e < m.Mrp * (m.M + 1); e += kPT) Bd[e] = (double)Bf[e];
@@ -484,9 +554,20 @@ extern "C" int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **ou
     m->h_idx.assign(s.idx, s.idx + L);
     m->ox = s.x0_s[0];
     m->oy = s.x0_s[s.n_s];
+    d.nlist = L;
+    constexpr size_t kSmemCap = 220 * 1024;
     const SmemLayout lay = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64);
     m->smem = lay.total;
-    if (m->smem > 220 * 1024) {
+    // stage constant rows / lists in shared memory when they fit
+    if (smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, 1, 0, L).total <= kSmemCap) {
+        d.cache_rows = 1;
+        m->smem = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, 1, 0, L).total;
+    }
+    if (d.Nc <= 65535 && smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, d.cache_rows, 1, L).total <= kSmemCap) {
+        d.cache_idx = 1;
+        m->smem = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, d.cache_rows, 1, L).total;
+    }
+    if (m->smem > kSmemCap) {
         delete m;
         return set_error(PTROM_EINVAL, "ptrom_model_create: model needs %zu bytes of shared memory", lay.total);
     }

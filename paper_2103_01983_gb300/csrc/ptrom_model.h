@@ -23,6 +23,9 @@ struct DevModel {
     const float *gT;    // [Nc]    Gamma~ / (2 pi)
     const int *off, *idx;
     const float *At;    // [2ns][Mrp]  (A transposed, zero padded)
+    int nlist;          // off[ns]: cluster-list entries
+    int cache_rows;     // Phi_s and A^T staged in shared memory for the whole launch
+    int cache_idx;      // the cluster lists staged in shared memory as 16-bit indices
 };
 
 struct InstArgs {
