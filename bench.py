@@ -306,6 +306,8 @@ def run_ours(args):
         line["ptrom"] = ptrom_leg(ptrom, dev, ms_all / args.steps)
     if rank == 0 and not args.no_batch:
         line["batched"] = batch_leg(ptrom, dev)
+    if rank == 0 and args.vortex_pair:
+        line["vortex_pair"] = vortex_pair_leg(ptrom, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
@@ -413,6 +415,68 @@ def ptrom_leg(ptrom, dev, fom_ms_per_step, steps=200):
         }
         del model
     return out
+
+
+def vortex_pair_leg(ptrom, dev):
+    """The paper's vortex-pair parametric experiment (Sec. 6.2) end to end:
+    PTROM trained at 4 Latin-hypercube parameters, queried on the 6 x 6 grid;
+    time-averaged QoI errors against the GPU FOM at each query, and the
+    PTROM-vs-FOM step speed-up (GPU FOM step time / GPU PTROM step time)."""
+    import numpy as np
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    V = W.VORTEX_PAIR
+    n, delta, dt, steps = V["n"], V["delta"], V["dt"], V["steps"]
+    train, query = W.vortex_pair_params(0)
+    fp = ptrom.fom_params(dt, delta, "jfnk", tol=1e-12, prec="fp64", gmres_rtol=1e-10, gmres_max_iter=400)
+    xs, gs = zip(*[W.vortex_pair(a, b) for a, b in train])
+    t0 = time.perf_counter()
+    model, info = ptrom.ptrom_build(torch.tensor(np.stack(xs), device=dev), torch.tensor(np.stack(gs), device=dev),
+                                    85, 110, 60, steps, fp, criterion="nb", p_c=1.0, tol=1e-4, qr_prec="fp64")
+    build_s = time.perf_counter() - t0
+    l = float(np.hypot(2 * V["half_width"], 2 * V["half_width"]))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for g1, gN in query:
+        x0, G = W.vortex_pair(g1, gN)
+        x = torch.tensor(x0, device=dev)
+        Gd = torch.tensor(G, device=dev)
+        f = ptrom.bs_velocity(x, Gd, delta, prec="fp64")
+        work = ptrom.fom_workspace(fp, n, dev)
+        fom = torch.empty(steps, 2 * n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for k in range(steps):
+            ptrom.fom_step(fp, Gd, x, f, work=work)
+            fom[k] = x
+        e1.record()
+        torch.cuda.synchronize(dev)
+        fom_ms = e0.elapsed_time(e1)
+        model.set_param_full(torch.tensor(x0, device=dev), Gd)
+        st = model.new_state(dev)
+        hist = torch.zeros(steps, model.M, dtype=torch.float64, device=dev)
+        e0.record()
+        ptrom.ptrom_step([model], [st], steps, hist=[hist], want_stats=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        rom_ms = e0.elapsed_time(e1)
+        rec = torch.stack([model.reconstruct(hist[k]) for k in range(steps)])
+        mae = float((torch.sqrt((rec[:, :n] - fom[:, :n]) ** 2 + (rec[:, n:] - fom[:, n:]) ** 2).mean(dim=1) / l).mean())
+        ks = list(range(0, steps, 25))
+        aeh = float(np.mean([abs(_hamiltonian_gpu(rec[k], Gd, n) - _hamiltonian_gpu(fom[k], Gd, n))
+                             / abs(_hamiltonian_gpu(fom[k], Gd, n)) for k in ks]))
+        rows.append((float(g1), float(gN), mae, aeh, fom_ms / rom_ms))
+    r = np.array(rows)
+    return {"workload": "vortex pair, N=500, delta=0.2121, dt=0.01, 500 steps; trained at 4 LHS parameters, "
+                        "queried on the 6x6 grid; M=85, M_r=110, 60 sampled bodies, neighbour p_c=1, FP64 QR",
+            "build_s": build_s, "N_c": info["N_c"], "paper_N_c": 233,
+            "mae_d_mean": float(r[:, 2].mean()), "mae_d_max": float(r[:, 2].max()), "paper_mae_d_mean": 0.0136e-2,
+            "ae_h_mean": float(r[:, 3].mean()), "ae_h_max": float(r[:, 3].max()), "paper_ae_h_mean": 6.09e-6,
+            "speedup_vs_gpu_fom_step_mean": float(r[:, 4].mean()),
+            "paper_speedup_mean": 3.94, "paper_speedup_note": "pair-loop time ratio, MATLAB on one CPU core",
+            "queries": [[round(a, 2), round(b, 2), m, h, sp] for a, b, m, h, sp in rows]}
 
 
 def batch_leg(ptrom, dev):
@@ -587,6 +651,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ptrom", action="store_true", help="skip the PTROM speed-up leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--vortex-pair", action="store_true",
+                    help="also run the paper's vortex-pair parametric experiment (about 3 minutes)")
     ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")

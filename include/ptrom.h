@@ -290,7 +290,7 @@ int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *Gamma,
  *   off     [n_s + 1], idx [off[n_s]]: CSR lists, sampled body i interacts
  *                       with clusters idx[off[i] .. off[i+1])
  *   A       [M_r x n_d] row-major: the gappy operator [P Phi_r]^+
- * Limits: M <= 64, M_r <= 128, n_s <= 512, N_c <= 8192 (shared-memory
+ * Limits: M <= 128, M_r <= 256, n_s <= 512, N_c <= 8192 (shared-memory
  * resident per instance).
  * ------------------------------------------------------------------------ */
 typedef struct ptrom_model ptrom_model;

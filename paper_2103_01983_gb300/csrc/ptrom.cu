@@ -189,17 +189,14 @@ __device__ void hyperpair_residual(const DevModel &m, const float *phiB, const u
 
 // Phase C: B[:, 0..M-1] = A C (C = J Phi_s), B[:, M] = A r; B column-major
 // (ld Mrp), FP32.  Each tile of 16 bodies (32 dofs) stages its rows of A^T
-// and of C in shared memory with one cooperative round of loads.
-// phiB, At: the Phi_s and A^T rows (shared or global memory).
+// and of C in shared memory with one cooperative round of loads; threads own
+// 4x4 blocks of B (several each for large M, M_r) and add each tile's
+// contribution to them in shared memory.
 __device__ void assemble_lsq(const DevModel &m, const float *phiB, const float *At, const float *D, const float *r,
                              float *Ct, float *Ats, float *B) {
     const float h = (float)(0.5 * m.dt);
-    const int tilesM = m.Mp / 4, tilesR = m.Mrp / 4;
-    const int t = threadIdx.x;
-    const bool owner = t < tilesM * tilesR;
-    const int r0 = owner ? 4 * (t / tilesM) : 0, m0 = owner ? 4 * (t % tilesM) : 0;
-    float acc[4][4] = {};
-    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int tilesM = m.Mp / 4, tilesR = m.Mrp / 4, nblk = tilesM * tilesR;
+    for (int e = threadIdx.x; e < m.Mrp * (m.M + 1); e += kPT) B[e] = 0.f;
     for (int i0 = 0; i0 < m.ns; i0 += kTileB) {
         const int nbt = min(kTileB, m.ns - i0);
         // stage the tile's A^T rows (slot 2j = chi dof of body i0+j, 2j+1 = psi dof)
@@ -225,7 +222,10 @@ __device__ void assemble_lsq(const DevModel &m, const float *phiB, const float *
             Ct[slot * m.Mp + k] = val;
         }
         __syncthreads();
-        if (owner) {
+        for (int blk = threadIdx.x; blk < nblk; blk += kPT) {
+            const int r0 = 4 * (blk / tilesM), m0 = 4 * (blk % tilesM);
+            float acc[4][4] = {};
+            float bacc[4] = {0.f, 0.f, 0.f, 0.f};
             for (int j = 0; j < nbt; ++j) {
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
@@ -244,19 +244,17 @@ __device__ void assemble_lsq(const DevModel &m, const float *phiB, const float *
                     }
                 }
             }
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                if (r0 + x >= m.Mr) continue;
+#pragma unroll
+                for (int y = 0; y < 4; ++y)
+                    if (m0 + y < m.M) B[(size_t)(m0 + y) * m.Mrp + r0 + x] += acc[x][y];
+                if (m0 == 0) B[(size_t)m.M * m.Mrp + r0 + x] += bacc[x];
+            }
         }
         __syncthreads();
     }
-    if (owner) {
-#pragma unroll
-        for (int x = 0; x < 4; ++x) {
-#pragma unroll
-            for (int y = 0; y < 4; ++y)
-                if (m0 + y < m.M) B[(size_t)(m0 + y) * m.Mrp + r0 + x] = (r0 + x < m.Mr) ? acc[x][y] : 0.f;
-            if (m0 == 0) B[(size_t)m.M * m.Mrp + r0 + x] = (r0 + x < m.Mr) ? bacc[x] : 0.f;
-        }
-    }
-    __syncthreads();
 }
 
 // eps numerator: || (A C)^T (A r) || from B = [A C | A r] (before the QR).
@@ -346,15 +344,22 @@ __device__ void lsq_solve(const DevModel &m, T *B, double *dx) {
     // j's row i; R's diagonal is s_alpha), one shuffle and one FMA per step
     if (warp == 0) {
         const T *rhs = B + (size_t)M * ld;
-        T c0 = lane < ncols ? -rhs[lane] : (T)0, c1 = lane + 32 < ncols ? -rhs[lane + 32] : (T)0;
+        constexpr int kQ = kMaxM / 32;  // rows per lane
+        T c[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) c[q] = lane + 32 * q < ncols ? -rhs[lane + 32 * q] : (T)0;
         for (int j = ncols - 1; j >= 0; --j) {
-            const T cj = j < 32 ? __shfl_sync(0xffffffffu, c0, j) : __shfl_sync(0xffffffffu, c1, j - 32);
+            T own = c[0];
+#pragma unroll
+            for (int q = 1; q < kQ; ++q) own = (j >> 5) == q ? c[q] : own;
+            const T cj = __shfl_sync(0xffffffffu, own, j & 31);
             const T rjj = s_alpha[j];
             const T yj = rjj != 0 ? cj * ls_rcp(rjj) : (T)0;
             if (lane == (j & 31)) s_y[j] = yj;
             const T *cjc = B + (size_t)j * ld;
-            if (lane < j) c0 -= cjc[lane] * yj;
-            if (lane + 32 < j) c1 -= cjc[lane + 32] * yj;
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                if (lane + 32 * q < j) c[q] -= cjc[lane + 32 * q] * yj;
         }
     }
     __syncthreads();

@@ -653,7 +653,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     if (!p || !x0s || !gammas || !out) return set_error(PTROM_EINVAL, "ptrom_build: NULL argument");
     if (n < 2 || n > 65536 || n_params < 1 || p->steps < 1 || (long long)n_params * p->steps > 4096)
         return set_error(PTROM_EINVAL, "ptrom_build: sizes out of range (n=%d params=%d steps=%d)", n, n_params, p->steps);
-    if (p->M < 1 || p->M > 64 || p->M_r < 1 || p->M_r > 128 || p->n_s < 1 || p->n_s > std::min(512, n))
+    if (p->M < 1 || p->M > kMaxM || p->M_r < 1 || p->M_r > kMaxMr || p->n_s < 1 || p->n_s > std::min(kMaxNs, n))
         return set_error(PTROM_EINVAL, "ptrom_build: M/M_r/n_s out of range");
     if (p->criterion != PTROM_BARNES_HUT && p->criterion != PTROM_NEIGHBOR)
         return set_error(PTROM_EINVAL, "ptrom_build: bad criterion");

@@ -9,7 +9,7 @@
 namespace ptrom {
 
 constexpr int kPT = 512;  // threads per instance
-constexpr int kMaxM = 64, kMaxMr = 128, kMaxNs = 512, kMaxNc = 8192;
+constexpr int kMaxM = 128, kMaxMr = 256, kMaxNs = 512, kMaxNc = 8192;
 constexpr int kTileB = 16;  // bodies per A C tile (32 dofs)
 
 struct DevModel {

@@ -121,3 +121,32 @@ def two_vortex(d: float = 1.0, g1: float = 1.0, g2: float = 1.0):
     """Two point vortices on the chi axis, a distance d apart, centred at 0."""
     x = np.array([-0.5 * d, 0.5 * d, 0.0, 0.0], dtype=np.float64)
     return x, np.array([g1, g2], dtype=np.float64)
+
+
+# --------------------------------------------------------------- the paper's
+# vortex-pair experiment (Sec. 6.2): N bodies evenly spaced on the diagonal
+# from (-52.93, -52.93) to (52.93, 52.93); the two end bodies carry the
+# parameter circulations mu = (Gamma_1, Gamma_N) in [0.25, 1] x Gamma_max
+# (Gamma_max = 255), every other body 0.01; delta = 0.2121 (the initial axis
+# spacing), dt = 0.01, t in [0, 5].
+VORTEX_PAIR = {"n": 500, "half_width": 52.93, "gamma_max": 255.0, "gamma_weak": 0.01, "delta": 0.2121,
+               "dt": 0.01, "steps": 500, "lo": 0.25}
+
+
+def vortex_pair(g1: float, gN: float, n: int = VORTEX_PAIR["n"]):
+    """State [chi..., psi...] and circulations of the vortex-pair experiment."""
+    s = np.linspace(-VORTEX_PAIR["half_width"], VORTEX_PAIR["half_width"], n)
+    x = np.concatenate([s, s])
+    G = np.full(n, VORTEX_PAIR["gamma_weak"])
+    G[0], G[-1] = g1, gN
+    return x, G
+
+
+def vortex_pair_params(seed: int = 0):
+    """Training mu (4 Latin-hypercube points) and the 6 x 6 query grid over
+    [lo, 1] x Gamma_max in both circulations (Sec. 6.2)."""
+    lo, gmax = VORTEX_PAIR["lo"], VORTEX_PAIR["gamma_max"]
+    train = lo * gmax + param_lhs(4, seed, (0.0, 1.0), (0.0, 1.0)) * (1.0 - lo) * gmax
+    g = np.linspace(lo * gmax, gmax, 6)
+    query = np.array([(a, b) for a in g for b in g])
+    return train, query
