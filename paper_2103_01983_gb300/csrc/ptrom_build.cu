@@ -514,13 +514,79 @@ void cluster_values(const std::vector<int> &mem, int n, int M, const double *phi
     x0c[1] = c / W;
 }
 
+// Covariance C = S S^T (nd x nd, upper triangle) of the nd x K column-major S.
+__global__ void k_cov(int nd, int K, const double *__restrict__ S, double *__restrict__ C) {
+    __shared__ double ta[32][33], tb[32][33];
+    const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
+    if (b0 < a0) return;  // upper triangle only (mirrored on the host)
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    double acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int q = ty; q < 32; q += 8) {  // rows a0.., b0.. of snapshots k0 + q (coalesced along the rows)
+            const int k = k0 + q;
+            ta[q][tx] = (k < K && a0 + tx < nd) ? S[(size_t)k * nd + a0 + tx] : 0.0;
+            tb[q][tx] = (k < K && b0 + tx < nd) ? S[(size_t)k * nd + b0 + tx] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 32; ++kk) {
+            const double bv = tb[kk][tx];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += ta[kk][ty + 8 * u] * bv;
+        }
+        __syncthreads();
+    }
+    for (int u = 0; u < 4; ++u) {
+        const int a = a0 + ty + 8 * u, b = b0 + tx;
+        if (a < nd && b < nd) C[(size_t)a * nd + b] = acc[u];
+    }
+}
+
 // POD of the nd x K column-major device matrix S: M leading modes (Phi host
-// [nd][M] row-major) and singular values, by the Gram matrix S^T S.
+// [nd][M] row-major) and singular values: by the Gram matrix S^T S (method of
+// snapshots) when there are fewer snapshots than dofs, else by the covariance
+// S S^T, whose eigenvectors are the modes themselves; the host eigensolver
+// then works on the smaller of the two (O(min(nd, K)^3)).
 // With clamp, M is lowered to the number of modes whose eigenvalue exceeds
 // 1e-24 of the largest (the numerical rank), instead of failing.
 int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vector<double> &Phi,
                std::vector<double> &sigma, bool clamp = false) {
     if (M > K) return set_error(PTROM_EINVAL, "ptrom_build: POD rank %d exceeds the %d snapshots", M, K);
+    if (nd < K) {
+        double *C = nullptr;
+        PTROM_TRY(scratch_alloc((void **)&C, sizeof(double) * (size_t)nd * nd, st));
+        dim3 grid((nd + 31) / 32, (nd + 31) / 32);
+        k_cov<<<grid, 256, 0, st>>>(nd, K, S, C);
+        count_launch();
+        std::vector<double> Ch((size_t)nd * nd);
+        PTROM_CUDA(cudaMemcpyAsync(Ch.data(), C, sizeof(double) * Ch.size(), cudaMemcpyDeviceToHost, st));
+        PTROM_CUDA(cudaStreamSynchronize(st));
+        PTROM_TRY(scratch_free(C, st));
+        for (int a = 0; a < nd; ++a)
+            for (int b = 0; b < a; ++b) Ch[(size_t)a * nd + b] = Ch[(size_t)b * nd + a];
+        std::vector<double> w, V;
+        if (!symeig(nd, Ch, w, V)) jacobi_eig(nd, Ch, w, V);
+        if (clamp) {
+            int r = 0;
+            while (r < M && w[r] > 1e-24 * w[0]) ++r;
+            M = std::max(r, 1);
+        }
+        sigma.resize(M);
+        Phi.resize((size_t)nd * M);
+        for (int m = 0; m < M; ++m) {
+            if (!(w[m] > 0.0)) return set_error(PTROM_EINVAL, "ptrom_build: POD rank %d exceeds the snapshot rank", M);
+            sigma[m] = sqrt(w[m]);
+            for (int d = 0; d < nd; ++d) Phi[(size_t)d * M + m] = V[(size_t)d * nd + m];
+        }
+        for (int m = 0; m < M; ++m) {  // sign convention: each column's largest-magnitude entry is positive
+            int best = 0;
+            for (int d = 1; d < nd; ++d)
+                if (fabs(Phi[(size_t)d * M + m]) > fabs(Phi[(size_t)best * M + m])) best = d;
+            if (Phi[(size_t)best * M + m] < 0)
+                for (int d = 0; d < nd; ++d) Phi[(size_t)d * M + m] = -Phi[(size_t)d * M + m];
+        }
+        return PTROM_OK;
+    }
     double *G = nullptr, *Wd = nullptr, *Pd = nullptr;
     PTROM_TRY(scratch_alloc((void **)&G, sizeof(double) * (size_t)K * K, st));
     dim3 grid((K + 31) / 32, (K + 31) / 32);

@@ -150,3 +150,22 @@ def vortex_pair_params(seed: int = 0):
     g = np.linspace(lo * gmax, gmax, 6)
     query = np.array([(a, b) for a in g for b in g])
     return train, query
+
+
+# --------------------------------------------------------------- the paper's
+# single-vortex reproductive experiment (Sec. 6.4, Table 1): N bodies on the
+# line linspace(-N, N, N) in both coordinates, delta = 0, every body 0.01
+# except the centre body (index N // 2), which carries Gamma_center; dt and
+# the time range per N, 2000 steps in every case.
+SINGLE_VORTEX = {  # N: (dt, Gamma_center, t_final)
+    100: (0.01, 500.0, 20.0), 500: (2.5e-3, 1e4, 5.0), 1000: (2.5e-4, 1e5, 0.5), 2000: (1.25e-4, 2e5, 0.25),
+    3000: (1e-4, 3e5, 0.2), 4000: (7.5e-5, 4e5, 0.15), 5000: (5e-5, 6.75e5, 0.1)}
+
+
+def single_vortex(n: int):
+    """State [chi..., psi...], circulations, dt and step count of Table 1's case n."""
+    dt, gc, tf = SINGLE_VORTEX[n]
+    s = np.linspace(-float(n), float(n), n)
+    G = np.full(n, 0.01)
+    G[n // 2] = gc
+    return np.concatenate([s, s]), G, dt, int(round(tf / dt))

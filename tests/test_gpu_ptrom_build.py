@@ -170,3 +170,19 @@ def test_save_load_desc_model(P, tmp_path):
         return xh
 
     assert torch.equal(run(m), run(back))
+
+
+def test_pod_more_snapshots_than_dofs_matches_oracle(P):
+    """With more snapshots than dofs (2n = 128 < 300 snapshots) the POD runs
+    on the covariance S S^T instead of the Gram matrix; it must give the
+    oracle's SVD modes and singular values all the same."""
+    x0, G = W.disk(64, seed=2)
+    steps, M = 300, 10
+    fp = P.fom_params(0.01, 0.05, "dense", tol=1e-12, prec="fp64")
+    model, info = P.ptrom_build(_dev(x0)[None], _dev(G)[None], M, 12, 12, steps, fp, criterion="bh", theta=0.5)
+    q = model.query()
+    traj, _ = fom.rollout(x0, G, 0.05, 0.01, steps, mode="dense", tol=1e-12)
+    Phi, sig = rom.pod(traj[1:].T, M)
+    np.testing.assert_allclose(q["sigma"], sig, rtol=1e-8)
+    assert np.abs(q["phi"] @ q["phi"].T - Phi @ Phi.T).max() <= 1e-8
+    assert info["n_snapshots"] == steps
