@@ -354,7 +354,10 @@ int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
  * parameters mu_p (circulations Gamma_p, initial states x0_p):
  *   Stage 1  FOM snapshots: the states x^n(mu_p), n = 1..steps (fom_step
  *            with the given FOM parameters), as Sec. 3.1 defines them;
- *   Stage 2  POD Phi (M modes, Sec. 3.1) of all snapshots; the quadtree of
+ *   Stage 2  POD Phi (M modes, Sec. 3.1) of all snapshots (exact: the
+ *            eigenvectors of the smaller of S^T S and S S^T; randomized range
+ *            finder with power iterations when min(2n, snapshots) exceeds
+ *            ptrom_set_pod_exact_max's bound, default 2048); the quadtree of
  *            the weighted POD space W = Phi sigma (Sec. 4.1.1) and the source
  *            clusters of every body (Alg. 2 with Alg. 3: Barnes-Hut theta or
  *            neighbour p_c);
@@ -366,9 +369,11 @@ int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
  * The returned online model is set to the first training parameter; use
  * ptrom_set_param_full for any other mu.
  * All input arrays are DEVICE arrays: x0s [n_params][2n], gammas
- * [n_params][n].  Limits of this build: n_params * steps <= 4096 snapshots,
- * n <= 65536.  Synchronises the stream (the host runs the tree and the small
- * dense algebra).
+ * [n_params][n].  Limits of this build: n_params * steps <= 65536 snapshots
+ * of at most 64 GB in all, n <= 65536; the residual snapshots keep up to 10
+ * Gauss-Newton iterates per step (up to 24 GB), later ones are dropped.
+ * Synchronises the stream (the host runs the tree and the small dense
+ * algebra).
  * ------------------------------------------------------------------------ */
 enum ptrom_criterion { PTROM_BARNES_HUT = 0, PTROM_NEIGHBOR = 1 };
 
@@ -396,6 +401,10 @@ typedef struct ptrom_build_info {
 int ptrom_build(const ptrom_build_params *p, int n, int n_params, const double *x0s,
                 const double *gammas, ptrom_model **out, ptrom_build_info *info,
                 ptrom_stream_t stream);
+
+/* POD method switch: exact eigensolve while min(2n, snapshots) <= n_max,
+ * randomized above (default 2048).  Process-wide.  PTROM_EINVAL for n < 1. */
+int ptrom_set_pod_exact_max(int n_max);
 
 /* Reload a built model for a new parameter from the full per-body arrays
  * (DEVICE, [2n] and [n]): cluster circulations, POD surrogates and reference

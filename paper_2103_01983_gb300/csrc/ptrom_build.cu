@@ -11,8 +11,12 @@
 #include <math.h>
 #include <string.h>
 
+#include <cublas_v2.h>
+
 #include <algorithm>
 #include <chrono>
+#include <mutex>
+#include <random>
 #include <unordered_map>
 #include <vector>
 
@@ -542,6 +546,128 @@ __global__ void k_cov(int nd, int K, const double *__restrict__ S, double *__res
     }
 }
 
+// ---------------------------------------------------------------- randomized POD
+// Above this size of min(nd, K) the POD uses a randomized range finder instead
+// of an exact host eigensolve of the Gram or covariance matrix.
+std::atomic<int> g_pod_exact_max{2048};
+
+#define PTROM_CUBLAS(call)                                                              \
+    do {                                                                                \
+        const cublasStatus_t _b = (call);                                               \
+        if (_b != CUBLAS_STATUS_SUCCESS)                                                \
+            return set_error(PTROM_ECUDA, "%s: cuBLAS status %d", #call, (int)_b);      \
+    } while (0)
+
+// A cuBLAS handle per device (created on first use), bound to `st`.
+static int cublas_for(cudaStream_t st, cublasHandle_t *out) {
+    static std::mutex mu;
+    static cublasHandle_t hs[64] = {};
+    int dev = 0;
+    PTROM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(PTROM_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!hs[dev]) PTROM_CUBLAS(cublasCreate(&hs[dev]));
+    PTROM_CUBLAS(cublasSetStream(hs[dev], st));
+    *out = hs[dev];
+    return PTROM_OK;
+}
+
+// Orthonormalise the m x r column-major device block A in place (SVQB: with
+// A^T A = V L V^T, A <- A V L^{-1/2}), dropping directions whose eigenvalue is
+// below 1e-20 of the largest; r may shrink.  T: m x r scratch.
+static int svqb(cublasHandle_t h, int m, int &r, double *A, double *T, double *Gd, double *Wd, cudaStream_t st) {
+    const double one = 1.0, zero = 0.0;
+    PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, r, r, m, &one, A, m, A, m, &zero, Gd, r));
+    std::vector<double> G((size_t)r * r), w, V;
+    PTROM_CUDA(cudaMemcpyAsync(G.data(), Gd, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, st));
+    PTROM_CUDA(cudaStreamSynchronize(st));
+    if (!symeig(r, G, w, V)) jacobi_eig(r, G, w, V);
+    int keep = 0;
+    while (keep < r && w[keep] > 1e-20 * w[0]) ++keep;
+    if (keep == 0) return set_error(PTROM_EINVAL, "ptrom_build: POD range block has rank 0");
+    std::vector<double> W((size_t)r * keep);  // column-major r x keep
+    for (int j = 0; j < keep; ++j)
+        for (int i = 0; i < r; ++i) W[(size_t)j * r + i] = V[(size_t)i * r + j] / sqrt(w[j]);
+    PTROM_CUDA(cudaMemcpyAsync(Wd, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, st));
+    PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, keep, r, &one, A, m, Wd, r, &zero, T, m));
+    PTROM_CUDA(cudaMemcpyAsync(A, T, sizeof(double) * (size_t)m * keep, cudaMemcpyDeviceToDevice, st));
+    r = keep;
+    return PTROM_OK;
+}
+
+// Randomized POD (range finder with two power iterations, each step
+// orthonormalised twice; then the exact SVD of the small projected block):
+// M leading modes of S (nd x K) to ~machine precision for the fast-decaying
+// spectra of snapshot matrices, with O(nd K (M + 32)) GEMM work on the GPU and
+// O((M + 32)^3) on the host.
+static int pod_randomized(int nd, int K, const double *S, int &M, cudaStream_t st, std::vector<double> &Phi,
+                          std::vector<double> &sigma, bool clamp) {
+    cublasHandle_t h;
+    PTROM_TRY(cublas_for(st, &h));
+    int r = std::min(M + 32, std::min(nd, K));
+    const int r0 = r;
+    double *Om, *Y, *Z, *T, *Gd, *Wd, *Bm;
+    PTROM_TRY(scratch_alloc((void **)&Om, sizeof(double) * (size_t)K * r0, st));
+    PTROM_TRY(scratch_alloc((void **)&Y, sizeof(double) * (size_t)nd * r0, st));
+    PTROM_TRY(scratch_alloc((void **)&Z, sizeof(double) * (size_t)K * r0, st));
+    PTROM_TRY(scratch_alloc((void **)&T, sizeof(double) * (size_t)std::max(nd, K) * r0, st));
+    PTROM_TRY(scratch_alloc((void **)&Gd, sizeof(double) * (size_t)r0 * r0, st));
+    PTROM_TRY(scratch_alloc((void **)&Wd, sizeof(double) * (size_t)r0 * r0, st));
+    PTROM_TRY(scratch_alloc((void **)&Bm, sizeof(double) * (size_t)r0 * K, st));
+    {
+        std::vector<double> om((size_t)K * r0);
+        std::mt19937_64 rng(20210302ull);
+        std::normal_distribution<double> normal(0.0, 1.0);
+        for (double &v : om) v = normal(rng);
+        PTROM_CUDA(cudaMemcpyAsync(Om, om.data(), sizeof(double) * om.size(), cudaMemcpyHostToDevice, st));
+        PTROM_CUDA(cudaStreamSynchronize(st));
+    }
+    const double one = 1.0, zero = 0.0;
+    PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nd, r, K, &one, S, nd, Om, K, &zero, Y, nd));
+    for (int pass = 0; pass < 2; ++pass) PTROM_TRY(svqb(h, nd, r, Y, T, Gd, Wd, st));
+    for (int it = 0; it < 2; ++it) {
+        PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, K, r, nd, &one, S, nd, Y, nd, &zero, Z, K));
+        for (int pass = 0; pass < 2; ++pass) PTROM_TRY(svqb(h, K, r, Z, T, Gd, Wd, st));
+        PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nd, r, K, &one, S, nd, Z, K, &zero, Y, nd));
+        for (int pass = 0; pass < 2; ++pass) PTROM_TRY(svqb(h, nd, r, Y, T, Gd, Wd, st));
+    }
+    // B = Y^T S (r x K); its left singular vectors by the eigenvectors of B B^T
+    PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, r, K, nd, &one, Y, nd, S, nd, &zero, Bm, r));
+    PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, r, r, K, &one, Bm, r, Bm, r, &zero, Gd, r));
+    std::vector<double> G((size_t)r * r), w, V;
+    PTROM_CUDA(cudaMemcpyAsync(G.data(), Gd, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, st));
+    PTROM_CUDA(cudaStreamSynchronize(st));
+    if (!symeig(r, G, w, V)) jacobi_eig(r, G, w, V);
+    if (clamp) {
+        int q = 0;
+        while (q < M && q < r && w[q] > 1e-24 * w[0]) ++q;
+        M = std::max(q, 1);
+    }
+    if (M > r) return set_error(PTROM_EINVAL, "ptrom_build: POD rank %d exceeds the snapshot rank %d", M, r);
+    sigma.resize(M);
+    std::vector<double> Vm((size_t)r * M);  // column-major r x M
+    for (int m = 0; m < M; ++m) {
+        if (!(w[m] > 0.0)) return set_error(PTROM_EINVAL, "ptrom_build: POD rank %d exceeds the snapshot rank", M);
+        sigma[m] = sqrt(w[m]);
+        for (int i = 0; i < r; ++i) Vm[(size_t)m * r + i] = V[(size_t)i * r + m];
+    }
+    PTROM_CUDA(cudaMemcpyAsync(Wd, Vm.data(), sizeof(double) * Vm.size(), cudaMemcpyHostToDevice, st));
+    PTROM_CUBLAS(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nd, M, r, &one, Y, nd, Wd, r, &zero, T, nd));
+    std::vector<double> P((size_t)nd * M);
+    PTROM_CUDA(cudaMemcpyAsync(P.data(), T, sizeof(double) * P.size(), cudaMemcpyDeviceToHost, st));
+    PTROM_CUDA(cudaStreamSynchronize(st));
+    for (double *b : {Om, Y, Z, T, Gd, Wd, Bm}) PTROM_TRY(scratch_free(b, st));
+    Phi.resize((size_t)nd * M);
+    for (int m = 0; m < M; ++m) {
+        int best = 0;
+        for (int d = 1; d < nd; ++d)
+            if (fabs(P[(size_t)m * nd + d]) > fabs(P[(size_t)m * nd + best])) best = d;
+        const double sgn = P[(size_t)m * nd + best] < 0 ? -1.0 : 1.0;  // largest-magnitude entry positive
+        for (int d = 0; d < nd; ++d) Phi[(size_t)d * M + m] = sgn * P[(size_t)m * nd + d];
+    }
+    return PTROM_OK;
+}
+
 // POD of the nd x K column-major device matrix S: M leading modes (Phi host
 // [nd][M] row-major) and singular values: by the Gram matrix S^T S (method of
 // snapshots) when there are fewer snapshots than dofs, else by the covariance
@@ -552,6 +678,7 @@ __global__ void k_cov(int nd, int K, const double *__restrict__ S, double *__res
 int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vector<double> &Phi,
                std::vector<double> &sigma, bool clamp = false) {
     if (M > K) return set_error(PTROM_EINVAL, "ptrom_build: POD rank %d exceeds the %d snapshots", M, K);
+    if (std::min(nd, K) > g_pod_exact_max.load()) return pod_randomized(nd, K, S, M, st, Phi, sigma, clamp);
     if (nd < K) {
         double *C = nullptr;
         PTROM_TRY(scratch_alloc((void **)&C, sizeof(double) * (size_t)nd * nd, st));
@@ -717,7 +844,8 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
                            const double *gammas, ptrom_model **out, ptrom_build_info *info,
                            ptrom_stream_t stream) {
     if (!p || !x0s || !gammas || !out) return set_error(PTROM_EINVAL, "ptrom_build: NULL argument");
-    if (n < 2 || n > 65536 || n_params < 1 || p->steps < 1 || (long long)n_params * p->steps > 4096)
+    if (n < 2 || n > 65536 || n_params < 1 || p->steps < 1 || (long long)n_params * p->steps > 65536 ||
+        (double)n_params * p->steps * 2 * n * 8 > 64e9)
         return set_error(PTROM_EINVAL, "ptrom_build: sizes out of range (n=%d params=%d steps=%d)", n, n_params, p->steps);
     if (p->M < 1 || p->M > kMaxM || p->M_r < 1 || p->M_r > kMaxMr || p->n_s < 1 || p->n_s > std::min(kMaxNs, n))
         return set_error(PTROM_EINVAL, "ptrom_build: M/M_r/n_s out of range");
@@ -837,17 +965,13 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     const double ox = x0h[0], oy = x0h[n];
     std::vector<float> phif((size_t)nd * Mp, 0.f), x0f(nd), phicf((size_t)2 * NcA * Mp, 0.f), x0cf(2 * (size_t)NcA),
         gcf(NcA);
-    for (int d = 0; d < nd; ++d) {
+    for (int d = 0; d < nd; ++d)
         for (int m = 0; m < M; ++m) phif[(size_t)d * Mp + m] = (float)Phi[(size_t)d * M + m];
-        x0f[d] = (float)(x0h[d] - (d < n ? ox : oy));
-    }
-    for (int rr = 0; rr < 2 * NcA; ++rr) {
-        for (int m = 0; m < M; ++m) phicf[(size_t)rr * Mp + m] = (float)phicA[(size_t)rr * M + m];
-        x0cf[rr] = (float)(x0cA[rr] - (rr < NcA ? ox : oy));
-    }
-    for (int c = 0; c < NcA; ++c) gcf[c] = (float)(gcA[c] * kInv2Pi);
     const int nblk = (n + kT2Bodies - 1) / kT2Bodies, nout = M * M + M;
-    const int maxres = std::min(4096, p->steps * std::max(p->max_gn, 1) * 1);
+    // residual snapshots kept (all Gauss-Newton iterates of every step and
+    // parameter, up to 24 GB of FP64 columns)
+    const long long want_res = (long long)n_params * p->steps * std::min(std::max(p->max_gn, 1), 10);
+    const int maxres = (int)std::min<long long>(std::min<long long>(want_res, 262144), (long long)(24e9 / (8.0 * nd)));
     // device buffers for Tier II
     float *dphi, *dx0, *dphic, *dx0c, *dgc, *dxt, *dpd, *dxq, *dxh, *ddx, *df, *dfp, *dD, *dr, *dpart;
     int *doff, *didx;
@@ -873,10 +997,6 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_TRY(scratch_alloc((void **)&dout, sizeof(double) * nout, st));
     PTROM_TRY(scratch_alloc((void **)&R, sizeof(double) * (size_t)nd * maxres, st));
     PTROM_CUDA(cudaMemcpyAsync(dphi, phif.data(), sizeof(float) * phif.size(), cudaMemcpyHostToDevice, st));
-    PTROM_CUDA(cudaMemcpyAsync(dx0, x0f.data(), sizeof(float) * nd, cudaMemcpyHostToDevice, st));
-    PTROM_CUDA(cudaMemcpyAsync(dphic, phicf.data(), sizeof(float) * phicf.size(), cudaMemcpyHostToDevice, st));
-    PTROM_CUDA(cudaMemcpyAsync(dx0c, x0cf.data(), sizeof(float) * x0cf.size(), cudaMemcpyHostToDevice, st));
-    PTROM_CUDA(cudaMemcpyAsync(dgc, gcf.data(), sizeof(float) * NcA, cudaMemcpyHostToDevice, st));
     PTROM_CUDA(cudaMemcpyAsync(doff, all.off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
     if (!all.idx.empty())
         PTROM_CUDA(cudaMemcpyAsync(didx, all.idx.data(), sizeof(int) * all.idx.size(), cudaMemcpyHostToDevice, st));
@@ -889,6 +1009,41 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     std::vector<float> xhf(Mp, 0.f), dxf(Mp, 0.f);
     std::vector<double> xh(M, 0.0), xprev(M), outh(nout);
     int nres = 0;
+    // Tier II for every training parameter: its reference state, and the
+    // cluster values recomputed from the stored memberships (as Sec. 5.2
+    // reloads them), each run from xhat = 0
+    std::vector<double> xq(nd), Gq(n), phicQ((size_t)2 * NcA * M), x0cQ(2 * (size_t)NcA), gcQ(NcA);
+    for (int q = 0; q < n_params; ++q) {
+    if (q == 0) {
+        xq = x0h;
+        Gq = Gh;
+        phicQ = phicA;
+        x0cQ = x0cA;
+        gcQ = gcA;
+    } else {
+        PTROM_CUDA(cudaMemcpyAsync(xq.data(), x0s + (size_t)q * nd, sizeof(double) * nd, cudaMemcpyDeviceToHost, st));
+        PTROM_CUDA(cudaMemcpyAsync(Gq.data(), gammas + (size_t)q * n, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        PTROM_CUDA(cudaStreamSynchronize(st));
+        for (int c = 0; c < NcA; ++c) {
+            key_members(T, all.keys[c], mem);
+            double xc[2];
+            cluster_values(mem, n, M, Phi.data(), xq.data(), Gq.data(), &phicQ[(size_t)c * M],
+                           &phicQ[(size_t)(NcA + c) * M], xc, &gcQ[c]);
+            x0cQ[c] = xc[0];
+            x0cQ[NcA + c] = xc[1];
+        }
+    }
+    for (int d = 0; d < nd; ++d) x0f[d] = (float)(xq[d] - (d < n ? ox : oy));
+    for (int rr = 0; rr < 2 * NcA; ++rr) {
+        for (int m = 0; m < M; ++m) phicf[(size_t)rr * Mp + m] = (float)phicQ[(size_t)rr * M + m];
+        x0cf[rr] = (float)(x0cQ[rr] - (rr < NcA ? ox : oy));
+    }
+    for (int c = 0; c < NcA; ++c) gcf[c] = (float)(gcQ[c] * kInv2Pi);
+    PTROM_CUDA(cudaMemcpyAsync(dx0, x0f.data(), sizeof(float) * nd, cudaMemcpyHostToDevice, st));
+    PTROM_CUDA(cudaMemcpyAsync(dphic, phicf.data(), sizeof(float) * phicf.size(), cudaMemcpyHostToDevice, st));
+    PTROM_CUDA(cudaMemcpyAsync(dx0c, x0cf.data(), sizeof(float) * x0cf.size(), cudaMemcpyHostToDevice, st));
+    PTROM_CUDA(cudaMemcpyAsync(dgc, gcf.data(), sizeof(float) * NcA, cudaMemcpyHostToDevice, st));
+    std::fill(xh.begin(), xh.end(), 0.0);
     // f~ at xhat = 0 (R11)
     PTROM_CUDA(cudaMemsetAsync(dxh, 0, sizeof(float) * Mp, st));
     PTROM_CUDA(cudaMemsetAsync(ddx, 0, sizeof(float) * Mp, st));
@@ -940,6 +1095,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
         }
         PTROM_CUDA(cudaMemcpyAsync(dfp, df, sizeof(float) * nd, cudaMemcpyDeviceToDevice, st));
     }
+    }  // training parameters
     PTROM_CUDA(cudaStreamSynchronize(st));
     inf.n_res_snapshots = nres;
     inf.seconds_tier2 = secs(t0);
@@ -1063,6 +1219,12 @@ int ptrom::model_store_basis(ptrom_model *m, const double *phi, const double *x0
     m->x0_dev = (double *)pd;
     if (cudaMemcpy(pd, x0, sizeof(double) * nd, cudaMemcpyHostToDevice) != cudaSuccess) return PTROM_ECUDA;
     m->x0_full.assign(x0, x0 + nd);
+    return PTROM_OK;
+}
+
+extern "C" int ptrom_set_pod_exact_max(int n) {
+    if (n < 1) return set_error(PTROM_EINVAL, "ptrom_set_pod_exact_max: n=%d must be >= 1", n);
+    g_pod_exact_max.store(n);
     return PTROM_OK;
 }
 

@@ -134,6 +134,7 @@ def _load():
         "bs_velocity_batched": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
         "fom_step_batched": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(FomStats), _vp], _i),
+        "ptrom_set_pod_exact_max": ([_i], _i),
         "ptrom_save": ([_vp, ctypes.c_char_p], _i),
         "ptrom_load": ([ctypes.c_char_p, ctypes.POINTER(_vp)], _i),
         "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
@@ -212,6 +213,11 @@ def timing_read() -> dict:
     cnt = (ctypes.c_longlong * k)()
     _check(lib.ptrom_timing_read(ms, cnt, k))
     return {name: (ms[i], int(cnt[i])) for i, name in enumerate(KERNEL_KINDS)}
+
+
+def set_pod_exact_max(n: int) -> None:
+    """POD: exact eigensolve up to min(2n, snapshots) = n, randomized above."""
+    _check(lib.ptrom_set_pod_exact_max(int(n)))
 
 
 def set_source_split(S: int) -> None:

@@ -186,3 +186,61 @@ def test_pod_more_snapshots_than_dofs_matches_oracle(P):
     np.testing.assert_allclose(q["sigma"], sig, rtol=1e-8)
     assert np.abs(q["phi"] @ q["phi"].T - Phi @ Phi.T).max() <= 1e-8
     assert info["n_snapshots"] == steps
+
+
+@pytest.mark.parametrize("steps", [100, 300])
+def test_randomized_pod_matches_oracle(P, steps):
+    """The randomized POD (range finder, two power iterations, forced here by
+    a small exact-size bound) gives the oracle's SVD modes and singular
+    values, with fewer (300) and with more (100 < 2n) snapshots than dofs."""
+    x0, G = W.disk(64, seed=2)
+    M = 10
+    fp = P.fom_params(0.01, 0.05, "dense", tol=1e-12, prec="fp64")
+    P.set_pod_exact_max(32)
+    try:
+        model, _ = P.ptrom_build(_dev(x0)[None], _dev(G)[None], M, 12, 12, steps, fp, criterion="bh", theta=0.5)
+    finally:
+        P.set_pod_exact_max(2048)
+    q = model.query()
+    traj, _ = fom.rollout(x0, G, 0.05, 0.01, steps, mode="dense", tol=1e-12)
+    Phi, sig = rom.pod(traj[1:].T, M)
+    np.testing.assert_allclose(q["sigma"], sig, rtol=1e-8)
+    assert np.abs(q["phi"] @ q["phi"].T - Phi @ Phi.T).max() <= 1e-8
+
+
+def test_tier2_collects_residuals_of_every_training_parameter(P):
+    """Stage 3 runs the Tier-II LSPG once per training parameter (each from
+    its own reference state and cluster values), so the residual snapshots
+    count every parameter's Gauss-Newton iterates and the hyper-reduced model
+    reproduces the FOM at the second training parameter as well as at the
+    first."""
+    x0, G = W.two_cluster(512, seed=0)
+    x1 = x0.copy()
+    x1[:512] *= 1.05
+    G1 = 0.8 * G
+    steps = 60
+    fp = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c")
+    model, info = P.ptrom_build(_dev(np.stack([x0, x1])), _dev(np.stack([G, G1])), 30, 60, 60, steps, fp,
+                                theta=0.0)
+    assert info["n_snapshots"] == 2 * steps
+    assert info["n_res_snapshots"] >= 2 * steps
+    errs = []
+    for xa, Ga in ((x0, G), (x1, G1)):
+        x = _dev(xa)
+        Gt = _dev(Ga)
+        f = P.bs_velocity(x, Gt, 0.02)
+        work = P.fom_workspace(fp, 512)
+        ref = []
+        for _ in range(steps):
+            P.fom_step(fp, Gt, x, f, work=work)
+            ref.append(x.cpu().numpy())
+        model.set_param_full(_dev(xa), Gt)
+        st = model.new_state()
+        hist = torch.zeros(steps, 30, dtype=torch.float64, device="cuda")
+        s = P.ptrom_step([model], [st], steps, hist=[hist])
+        assert s["noconv"] == 0
+        rec = np.array([model.reconstruct(hist[k]).cpu().numpy() for k in range(steps)])
+        disp = np.abs(np.array(ref) - xa).max()
+        errs.append(np.abs(rec - np.array(ref)).max() / disp)
+    print("relative errors", errs)
+    assert max(errs) <= 1e-5, errs
