@@ -308,6 +308,8 @@ def run_ours(args):
         line["batched"] = batch_leg(ptrom, dev)
     if rank == 0 and args.vortex_pair:
         line["vortex_pair"] = vortex_pair_leg(ptrom, dev)
+    if rank == 0 and args.mushroom:
+        line["mushroom"] = mushroom_leg(ptrom, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
@@ -418,43 +420,76 @@ def ptrom_leg(ptrom, dev, fom_ms_per_step, steps=200):
 
 
 def vortex_pair_leg(ptrom, dev):
-    """The paper's vortex-pair parametric experiment (Sec. 6.2) end to end:
-    PTROM trained at 4 Latin-hypercube parameters, queried on the 6 x 6 grid;
-    time-averaged QoI errors against the GPU FOM at each query, and the
-    PTROM-vs-FOM step speed-up (GPU FOM step time / GPU PTROM step time)."""
+    """The paper's vortex-pair parametric experiment (Sec. 6.2); see
+    ``parametric_leg``."""
+    return parametric_leg(ptrom, dev, "vortex_pair")
+
+
+def mushroom_leg(ptrom, dev):
+    """The paper's mushroom-cloud parametric experiment (Sec. 6.3, with the
+    superimposed inflow); see ``parametric_leg``."""
+    return parametric_leg(ptrom, dev, "mushroom")
+
+
+def parametric_leg(ptrom, dev, which):
+    """One of the paper's parametric experiments end to end: PTROM trained at
+    4 Latin-hypercube parameters, queried on the 6 x 6 grid; time-averaged
+    QoI errors against the GPU FOM at each query, and the PTROM-vs-FOM step
+    speed-up (GPU FOM step time / GPU PTROM step time)."""
     import numpy as np
     import torch
 
     from paper_2103_01983_gb300 import workloads as W
 
-    V = W.VORTEX_PAIR
+    if which == "vortex_pair":
+        V = W.VORTEX_PAIR
+        train, query = W.vortex_pair_params(0)
+        setup = lambda a, b: (*W.vortex_pair(a, b), None)
+        M, Mr, ns = 85, 110, 60
+        paper = {"paper_N_c": 233, "paper_mae_d_mean": 0.0136e-2, "paper_ae_h_mean": 6.09e-6,
+                 "paper_speedup_mean": 3.94}
+        l = float(np.hypot(2 * V["half_width"], 2 * V["half_width"]))
+        desc = ("vortex pair, N=500, delta=0.2121, dt=0.01, 500 steps; trained at 4 LHS parameters, "
+                "queried on the 6x6 grid; M=85, M_r=110, 60 sampled bodies, neighbour p_c=1, FP64 QR")
+    else:
+        V = W.MUSHROOM
+        train, query = W.mushroom_params(0)
+        setup = W.mushroom
+        M, Mr, ns = 110, 185, 75
+        paper = {"paper_N_c": 294, "paper_mae_d_mean": 0.0634e-2, "paper_ae_h_mean": 2.39e-5,
+                 "paper_speedup_mean": 1.71}
+        l = 2 * V["half_width"]
+        desc = ("mushroom cloud, N=500, delta=0.15, dt=0.005, 1000 steps, semicircular inflow; trained at 4 LHS "
+                "parameters, queried on the 6x6 grid; M=110, M_r=185, 75 sampled bodies, neighbour p_c=1, FP64 QR")
     n, delta, dt, steps = V["n"], V["delta"], V["dt"], V["steps"]
-    train, query = W.vortex_pair_params(0)
     fp = ptrom.fom_params(dt, delta, "jfnk", tol=1e-12, prec="fp64", gmres_rtol=1e-10, gmres_max_iter=400)
-    xs, gs = zip(*[W.vortex_pair(a, b) for a, b in train])
+    xs, gs, us = zip(*[setup(a, b) for a, b in train])
     t0 = time.perf_counter()
     model, info = ptrom.ptrom_build(torch.tensor(np.stack(xs), device=dev), torch.tensor(np.stack(gs), device=dev),
-                                    85, 110, 60, steps, fp, criterion="nb", p_c=1.0, tol=1e-4, qr_prec="fp64")
+                                    M, Mr, ns, steps, fp, criterion="nb", p_c=1.0, tol=1e-4, qr_prec="fp64",
+                                    u_infs=None if us[0] is None else torch.tensor(np.stack(us), device=dev))
     build_s = time.perf_counter() - t0
-    l = float(np.hypot(2 * V["half_width"], 2 * V["half_width"]))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rows = []
     for g1, gN in query:
-        x0, G = W.vortex_pair(g1, gN)
+        x0, G, u = setup(g1, gN)
         x = torch.tensor(x0, device=dev)
         Gd = torch.tensor(G, device=dev)
+        ud = None if u is None else torch.tensor(u, device=dev)
         f = ptrom.bs_velocity(x, Gd, delta, prec="fp64")
         work = ptrom.fom_workspace(fp, n, dev)
         fom = torch.empty(steps, 2 * n, dtype=torch.float64, device=dev)
         torch.cuda.synchronize(dev)
         e0.record()
         for k in range(steps):
-            ptrom.fom_step(fp, Gd, x, f, work=work)
+            ptrom.fom_step(fp, Gd, x, f, work=work, u_inf=ud)
             fom[k] = x
         e1.record()
         torch.cuda.synchronize(dev)
         fom_ms = e0.elapsed_time(e1)
         model.set_param_full(torch.tensor(x0, device=dev), Gd)
+        if ud is not None:
+            model.set_inflow_full(ud)
         st = model.new_state(dev)
         hist = torch.zeros(steps, model.M, dtype=torch.float64, device=dev)
         e0.record()
@@ -469,13 +504,14 @@ def vortex_pair_leg(ptrom, dev):
                              / abs(_hamiltonian_gpu(fom[k], Gd, n)) for k in ks]))
         rows.append((float(g1), float(gN), mae, aeh, fom_ms / rom_ms))
     r = np.array(rows)
-    return {"workload": "vortex pair, N=500, delta=0.2121, dt=0.01, 500 steps; trained at 4 LHS parameters, "
-                        "queried on the 6x6 grid; M=85, M_r=110, 60 sampled bodies, neighbour p_c=1, FP64 QR",
-            "build_s": build_s, "N_c": info["N_c"], "paper_N_c": 233,
-            "mae_d_mean": float(r[:, 2].mean()), "mae_d_max": float(r[:, 2].max()), "paper_mae_d_mean": 0.0136e-2,
-            "ae_h_mean": float(r[:, 3].mean()), "ae_h_max": float(r[:, 3].max()), "paper_ae_h_mean": 6.09e-6,
+    return {"workload": desc, "build_s": build_s, "N_c": info["N_c"], "paper_N_c": paper["paper_N_c"],
+            "mae_d_mean": float(r[:, 2].mean()), "mae_d_max": float(r[:, 2].max()),
+            "paper_mae_d_mean": paper["paper_mae_d_mean"],
+            "ae_h_mean": float(r[:, 3].mean()), "ae_h_max": float(r[:, 3].max()),
+            "paper_ae_h_mean": paper["paper_ae_h_mean"],
             "speedup_vs_gpu_fom_step_mean": float(r[:, 4].mean()),
-            "paper_speedup_mean": 3.94, "paper_speedup_note": "pair-loop time ratio, MATLAB on one CPU core",
+            "paper_speedup_mean": paper["paper_speedup_mean"],
+            "paper_speedup_note": "pair-loop time ratio, MATLAB on one CPU core",
             "queries": [[round(a, 2), round(b, 2), m, h, sp] for a, b, m, h, sp in rows]}
 
 
@@ -653,6 +689,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--vortex-pair", action="store_true",
                     help="also run the paper's vortex-pair parametric experiment (about 3 minutes)")
+    ap.add_argument("--mushroom", action="store_true",
+                    help="also run the paper's mushroom-cloud parametric experiment (about 5 minutes)")
     ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")

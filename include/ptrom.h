@@ -184,6 +184,10 @@ int bs_jphi(int n, const double *x, const double *Gamma, double delta,
  * The Jacobian (self blocks / dense factors) is refreshed every p_it Newton
  * iterations.  Convergence: ||r||_2 <= tol * max(1, ||xi||_2), checked after
  * each evaluation of f(xi) (so the returned f is f at the returned state).
+ * Optional superimposed inflow u (Sec. 6.3: a constant velocity per body,
+ * dx/dt = f(x) + u): the residual becomes
+ *     r(xi) = xi - x^{n-1} - dt/2 (f(xi) + f(x^{n-1})) - dt u,
+ * the Jacobian is unchanged, and f (in/out) stays the pair sum of Eq. 2.
  * ------------------------------------------------------------------------ */
 enum ptrom_jac_mode { PTROM_JAC_BLOCKDIAG = 0, PTROM_JAC_DENSE = 1, PTROM_JAC_JFNK = 2 };
 
@@ -198,6 +202,10 @@ typedef struct ptrom_fom_params {
     int gmres_restart;  /* JFNK: Krylov vectors per cycle, 1..64             */
     int gmres_max_iter; /* JFNK: Krylov iterations per Newton step           */
     double gmres_rtol;  /* JFNK: relative linear tolerance                   */
+    const double *u_inf; /* superimposed inflow: DEVICE [2n] ([u_chi..., u_psi...])
+                            or NULL for none; fom_step_batched requires NULL,
+                            fom_adjoint_step ignores it (u does not depend on
+                            x or Gamma)                                      */
 } ptrom_fom_params;
 
 typedef struct ptrom_fom_stats {
@@ -304,6 +312,8 @@ typedef struct ptrom_model_desc {
     /* HOST arrays, copied into the model */
     const double *phi_s, *x0_s, *phi_c, *x0_c, *gamma_c, *A;
     const int *off, *idx;
+    const double *u_s;  /* [n_d] superimposed inflow at the sampled dofs (Sec. 6.3),
+                           or NULL for none: the residual gains -dt u_s        */
 } ptrom_model_desc;
 
 typedef struct ptrom_stats {
@@ -324,6 +334,11 @@ void ptrom_free(ptrom_model *m);
  * any may be NULL to keep the current one). */
 int ptrom_set_param(ptrom_model *m, const double *x0_s, const double *phi_c,
                     const double *x0_c, const double *gamma_c);
+
+/* Replace the superimposed inflow at the sampled dofs (HOST [n_d], or NULL
+ * to remove it).  Like the circulation, the inflow is a parameter that
+ * needs no retraining (Sec. 5.2). */
+int ptrom_set_inflow(ptrom_model *m, const double *u_s);
 
 /* Device bytes of per-instance online state for a model (xhat, the carried
  * velocity at the sampled dofs, flags). */
@@ -363,13 +378,16 @@ int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
  *            neighbour p_c);
  *   Stage 3  Tier-II LSPG (Eq. GNLinearLeastSquares) over all bodies with the
  *            clustered sources, the inexact block-diagonal Jacobian and
- *            alpha = 1, collecting the residual at every Gauss-Newton iterate;
+ *            alpha = 1, run once per training parameter (its x0_p and its
+ *            cluster values), collecting the residual at every Gauss-Newton
+ *            iterate;
  *            residual POD Phi_r (M_r modes);
  *   Stage 4  greedy sampling of n_s bodies (Alg. 1), A = [P Phi_r]^+.
  * The returned online model is set to the first training parameter; use
- * ptrom_set_param_full for any other mu.
+ * ptrom_set_param_full (and ptrom_set_inflow_full) for any other mu.
  * All input arrays are DEVICE arrays: x0s [n_params][2n], gammas
- * [n_params][n].  Limits of this build: n_params * steps <= 65536 snapshots
+ * [n_params][n], and p->u_infs [n_params][2n] (per-parameter superimposed
+ * inflow, or NULL; p->fom.u_inf is ignored).  Limits of this build: n_params * steps <= 65536 snapshots
  * of at most 64 GB in all, n <= 65536; the residual snapshots keep up to 10
  * Gauss-Newton iterates per step (up to 24 GB), later ones are dropped.
  * Synchronises the stream (the host runs the tree and the small dense
@@ -386,6 +404,7 @@ typedef struct ptrom_build_params {
     int max_gn;            /* Gauss-Newton cap (Tier II and online)          */
     int qr_prec;           /* online least-squares precision                 */
     ptrom_fom_params fom;  /* Stage 1 FOM (dt and delta are the model's)     */
+    const double *u_infs;  /* DEVICE [n_params][2n] inflow per parameter, or NULL */
 } ptrom_build_params;
 
 typedef struct ptrom_build_info {
@@ -412,6 +431,10 @@ int ptrom_set_pod_exact_max(int n_max);
  * retraining.  PTROM_EINVAL for models not made by ptrom_build. */
 int ptrom_set_param_full(ptrom_model *m, const double *x0, const double *Gamma,
                          ptrom_stream_t stream);
+
+/* Set a built model's superimposed inflow from the full per-body array
+ * (DEVICE [2n]; NULL removes it): its sampled rows become the model's u_s. */
+int ptrom_set_inflow_full(ptrom_model *m, const double *u, ptrom_stream_t stream);
 
 /* x = x^0 + Phi xhat on the listed bodies (Sec. 5.3): rows [nrows] (DEVICE
  * int body indices), out [2 nrows] ([chi..., psi...]), xhat [M] (DEVICE).

@@ -17,6 +17,12 @@ iterations, each solving (I - dt/2 J) delta = -r with J one of
 The Jacobian is refreshed every ``p_it`` Newton iterations (1 = every one).
 Convergence: ||r||_2 <= tol * max(1, ||xi||_2), tested right after f(xi) is
 evaluated, so the returned f is f at the returned state.
+
+Superimposed inflow (Sec. 6.3, and the inflow sweeps Sec. 5.2 mentions): a
+constant velocity u_i per body is added to the right-hand side,
+dx_i/dt = f_i(x) + u_i.  The trapezoid rule then averages u with itself, so
+the residual gains -dt u; u does not depend on x, so no Jacobian changes.
+``f`` stays the pair sum of Eq. 2 alone.
 """
 from __future__ import annotations
 
@@ -26,8 +32,11 @@ import scipy.sparse.linalg as spla
 from . import direct, kernel
 
 
-def residual(xi, x_prev, f_xi, f_prev, dt):
-    return xi - x_prev - 0.5 * dt * (f_xi + f_prev)
+def residual(xi, x_prev, f_xi, f_prev, dt, u_inf=None):
+    r = xi - x_prev - 0.5 * dt * (f_xi + f_prev)
+    if u_inf is not None:
+        r = r - dt * np.asarray(u_inf, dtype=np.float64)
+    return r
 
 
 def _blockdiag_solve(D, rhs, dt):
@@ -45,7 +54,7 @@ def _blockdiag_solve(D, rhs, dt):
 
 
 def step(x_prev, f_prev, Gamma, delta, dt, mode="dense", tol=1e-12, max_iter=100,
-         p_it=1, gmres_tol=1e-10, gmres_restart=30):
+         p_it=1, gmres_tol=1e-10, gmres_restart=30, u_inf=None):
     """One implicit trapezoid step.  Returns (x^n, f(x^n), iterations, ||r||)."""
     x_prev = np.asarray(x_prev, dtype=np.float64)
     n = x_prev.size // 2
@@ -57,7 +66,7 @@ def step(x_prev, f_prev, Gamma, delta, dt, mode="dense", tol=1e-12, max_iter=100
             f, D = direct.velocity(xi, Gamma, delta, with_selfjac=True)
         else:
             f = direct.velocity(xi, Gamma, delta)
-        r = residual(xi, x_prev, f, f_prev, dt)
+        r = residual(xi, x_prev, f, f_prev, dt, u_inf)
         rn = float(np.linalg.norm(r))
         if rn <= tol * max(1.0, float(np.linalg.norm(xi))) or k == max_iter:
             return xi, f, k, rn

@@ -302,10 +302,21 @@ def target_rows(Phi, x0, targets):
 
 
 # ------------------------------------------------------------------ Tier II
-def lspg_tier2(cl: Clusters, Phi, x0, delta, dt, steps, tol=1e-4, max_gn=100):
+def _inflow_rows(u_inf, targets, n_dofs):
+    """The targets' rows of the superimposed inflow u (Sec. 6.3), or 0."""
+    if u_inf is None:
+        return np.zeros(n_dofs)
+    u = np.asarray(u_inf, dtype=np.float64)
+    return u[np.concatenate([targets, u.size // 2 + np.asarray(targets)])]
+
+
+def lspg_tier2(cl: Clusters, Phi, x0, delta, dt, steps, tol=1e-4, max_gn=100, u_inf=None):
     """Stage 3: LSPG over all targets with clustered sources.  Returns the
-    reduced trajectory (steps+1, M) and the residual snapshots (R12)."""
+    reduced trajectory (steps+1, M) and the residual snapshots (R12).
+    u_inf: optional constant inflow velocity per dof (Sec. 6.3), added to
+    the right-hand side, so the residual gains -dt u at the targets."""
     Phi_t, x0_t = target_rows(Phi, x0, cl.targets)
+    u_t = _inflow_rows(u_inf, cl.targets, Phi_t.shape[0])
     M = Phi.shape[1]
     xhat = np.zeros(M)
     f_prev, _ = hyperpair(xhat, cl, Phi_t, x0_t, delta)
@@ -316,7 +327,7 @@ def lspg_tier2(cl: Clusters, Phi, x0, delta, dt, steps, tol=1e-4, max_gn=100):
         first = None
         for k in range(max_gn):
             f, D = hyperpair(xhat, cl, Phi_t, x0_t, delta)
-            r = Phi_t @ (xhat - xprev) - 0.5 * dt * (f + f_prev)
+            r = Phi_t @ (xhat - xprev) - 0.5 * dt * (f + f_prev) - dt * u_t
             snaps.append(r.copy())
             C = jacobian_rows(D, Phi_t, dt)
             dx = np.linalg.lstsq(C, -r, rcond=None)[0]
@@ -367,11 +378,12 @@ def gappy_operator(Phi_r, sampled, N):
 
 
 # ------------------------------------------------------------------ Alg. 4
-def ptrom_online(cl: Clusters, Phi, x0, A, delta, dt, steps, tol=1e-4, max_gn=100):
+def ptrom_online(cl: Clusters, Phi, x0, A, delta, dt, steps, tol=1e-4, max_gn=100, u_inf=None):
     """Online Gauss-Newton (Alg. 4) over HyperPair at the sampled bodies
     (cl.targets).  Returns the reduced trajectory (steps+1, M) and the
-    Gauss-Newton iteration counts."""
+    Gauss-Newton iteration counts.  u_inf: as in ``lspg_tier2``."""
     Phi_t, x0_t = target_rows(Phi, x0, cl.targets)
+    u_t = _inflow_rows(u_inf, cl.targets, Phi_t.shape[0])
     M = Phi.shape[1]
     xhat = np.zeros(M)
     f_prev, _ = hyperpair(xhat, cl, Phi_t, x0_t, delta)   # R11
@@ -383,7 +395,7 @@ def ptrom_online(cl: Clusters, Phi, x0, A, delta, dt, steps, tol=1e-4, max_gn=10
         k = 0
         while True:
             f, D = hyperpair(xhat, cl, Phi_t, x0_t, delta)
-            r = Phi_t @ (xhat - xprev) - 0.5 * dt * (f + f_prev)
+            r = Phi_t @ (xhat - xprev) - 0.5 * dt * (f + f_prev) - dt * u_t
             C = jacobian_rows(D, Phi_t, dt)
             AC, Ar = A @ C, A @ r                                    # R10
             dx = np.linalg.lstsq(AC, -Ar, rcond=None)[0]

@@ -91,18 +91,21 @@ __device__ __forceinline__ bool finish_reduction(const Red &red, int nk) {
     return true;
 }
 
-// r = xi - xprev - hdt (fxi + fprev);   out = {||r||^2, ||xi||^2}.
+// r = xi - xprev - hdt (fxi + fprev) [- dt u];   out = {||r||^2, ||xi||^2}.
+// u: the optional superimposed inflow (Sec. 6.3), constant per dof; the
+// trapezoid rule averages it with itself, so it enters as dt u = 2 hdt u.
 // The last block also takes the Newton decision (converged when
 // ||r|| <= tol max(1, ||xi||)): st = {stop, ||r||, ||xi||} with stop 0 = go on,
 // 1 = converged, 2 = non-finite residual, 3 = iteration limit (limit set);
 // flags[0] = (stop != 0) lets queued Newton-update kernels skip themselves.
 __global__ void k_residual(int n2, const double *xi, const double *xprev, const double *fxi,
-                           const double *fprev, double hdt, double *r, Red red, double tol, int limit, int *flags,
-                           double *st) {
+                           const double *fprev, const double *u, double hdt, double *r, Red red, double tol,
+                           int limit, int *flags, double *st) {
     __shared__ double sh[32];
     double s0 = 0.0, s1 = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
-        const double v = xi[i] - xprev[i] - hdt * (fxi[i] + fprev[i]);
+        double v = xi[i] - xprev[i] - hdt * (fxi[i] + fprev[i]);
+        if (u) v -= (2.0 * hdt) * u[i];
         r[i] = v;
         s0 += v * v;
         s1 += xi[i] * xi[i];
@@ -555,7 +558,7 @@ k_cgs2(int n, int K, const double *V, const double *w, double *partials, double 
 }
 
 // Newton residual of the trapezoid step in one cooperative kernel over
-// bodies: r = x - xprev - hdt (f(x) + fprev), ||r||^2 and ||x||^2 reduced in a
+// bodies: r = x - xprev - hdt (f(x) + fprev) [- dt u], ||r||^2 and ||x||^2 reduced in a
 // fixed order that every block repeats, the Newton test (converged when
 // ||r|| <= tol max(1, ||x||)) taken identically in every block.  Block 0 writes
 // st = {stop, ||r||, ||x||} (stop 0 go on, 1 converged, 2 non-finite, 3 at
@@ -568,6 +571,7 @@ struct NewtonArgs {
     int n;
     double *x, *xprev;
     const double *fxi, *fprev;
+    const double *u;  // superimposed inflow [2n] or nullptr
     double hdt;
     double *r, *partials, *redout;
     double tol;
@@ -614,8 +618,12 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
                 xp0 = a.xprev[i];
                 xp1 = a.xprev[n + i];
             }
-            const double v0 = x0 - xp0 - a.hdt * (a.fxi[i] + a.fprev[i]);
-            const double v1 = x1 - xp1 - a.hdt * (a.fxi[n + i] + a.fprev[n + i]);
+            double v0 = x0 - xp0 - a.hdt * (a.fxi[i] + a.fprev[i]);
+            double v1 = x1 - xp1 - a.hdt * (a.fxi[n + i] + a.fprev[n + i]);
+            if (a.u) {
+                v0 -= (2.0 * a.hdt) * a.u[i];
+                v1 -= (2.0 * a.hdt) * a.u[n + i];
+            }
             a.r[i] = v0;
             a.r[n + i] = v1;
             r0[e] = v0;
@@ -1252,7 +1260,7 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
         if (c.coop) {
             // residual, norms, Newton test, M^{-1} refresh and (block-diagonal)
             // the Newton update or (JFNK) v_0 and z in one cooperative launch
-            NewtonArgs na{n, x, W.xprev, W.fxi, f, c.hdt, W.r, W.partials, W.redout, p->tol,
+            NewtonArgs na{n, x, W.xprev, W.fxi, f, p->u_inf, c.hdt, W.r, W.partials, W.redout, p->tol,
                           k == p->max_iter, W.flags, W.stat, refresh ? 1 : 0, W.D, W.Mi,
                           p->jac_mode == PTROM_JAC_BLOCKDIAG ? 1 : (jfnk ? 2 : 0), W.V, W.z,
                           k == 0 ? 1 : 0, f, W.d, W.counter};
@@ -1269,7 +1277,7 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
                 count_launch();
             }
             PTROM_TIMED(PTROM_K_FOM_VEC, c.st, (Slots *)nullptr,
-                        k_residual<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, x, W.xprev, W.fxi, f, c.hdt, W.r,
+                        k_residual<<<c.rgrid, kRedThreads, 0, c.st>>>(c.n2, x, W.xprev, W.fxi, f, p->u_inf, c.hdt, W.r,
                                                                      mkred(W, 0), p->tol, k == p->max_iter, W.flags,
                                                                      W.stat));
             count_launch();
@@ -1464,6 +1472,7 @@ extern "C" int fom_step_batched(const ptrom_fom_params *p, int B, const int *n, 
         return set_error(PTROM_EINVAL, "fom_step_batched: bad arguments");
     if (p->jac_mode != PTROM_JAC_BLOCKDIAG)
         return set_error(PTROM_EINVAL, "fom_step_batched: only the block-diagonal (inexact) Jacobian is batched");
+    if (p->u_inf) return set_error(PTROM_EINVAL, "fom_step_batched: u_inf must be NULL (one inflow per instance)");
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<Work> W(B);
     for (int b = 0; b < B; ++b) {

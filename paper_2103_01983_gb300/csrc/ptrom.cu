@@ -138,7 +138,8 @@ __device__ __forceinline__ float row_dot(const float *row, const float *vec, int
 }
 
 // Phase B, warp per sampled body i: x~_i, the HyperPair sums f~_i and D~_i
-// over its clusters, and the residual r_i = Phi_s,i dxhat - h (f~_i + f~^{n-1}_i).
+// over its clusters, and the residual r_i = Phi_s,i dxhat - h (f~_i + f~^{n-1}_i)
+// - dt u_i (u: the superimposed inflow of Sec. 6.3, stored as dt u).
 // phiB: the Phi_s rows (shared or global memory); idx16: the cluster lists in
 // shared memory as 16-bit indices, or nullptr to read m.idx.
 __device__ void hyperpair_residual(const DevModel &m, const float *phiB, const unsigned short *idx16,
@@ -180,8 +181,8 @@ __device__ void hyperpair_residual(const DevModel &m, const float *phiB, const u
             D[i] = d00;
             D[m.ns + i] = d01;
             D[2 * m.ns + i] = -d10n;
-            r[i] = gx - h * (fx + fp[i]);
-            r[m.ns + i] = gy - h * (fy + fp[m.ns + i]);
+            r[i] = gx - h * (fx + fp[i]) - m.uB[i];
+            r[m.ns + i] = gy - h * (fy + fp[m.ns + i]) - m.uB[m.ns + i];
         }
     }
     __syncthreads();
@@ -519,6 +520,19 @@ int ptrom::model_fill_param(ptrom_model *m, const double *x0_s, const double *ph
     return PTROM_OK;
 }
 
+int ptrom::model_fill_inflow(ptrom_model *m, const double *u_s) {
+    const DevModel &d = m->d;
+    std::vector<float> v(2 * (size_t)d.ns, 0.f);
+    if (u_s) {
+        m->h_u_s.assign(u_s, u_s + 2 * (size_t)d.ns);
+        for (int e = 0; e < 2 * d.ns; ++e) v[e] = (float)(d.dt * u_s[e]);
+    } else {
+        m->h_u_s.clear();
+    }
+    PTROM_CUDA(cudaMemcpy((void *)d.uB, v.data(), v.size() * 4, cudaMemcpyHostToDevice));
+    return PTROM_OK;
+}
+
 extern "C" int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **out) {
     if (!desc || !out) return set_error(PTROM_EINVAL, "ptrom_model_create: NULL argument");
     const ptrom_model_desc &s = *desc;
@@ -595,6 +609,8 @@ extern "C" int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **ou
     d.x0T = (const float *)p;
     if ((st = upload(m, nullptr, (size_t)d.Nc * 4, &p))) return fail(st);
     d.gT = (const float *)p;
+    if ((st = upload(m, nullptr, 2 * (size_t)d.ns * 4, &p))) return fail(st);
+    d.uB = (const float *)p;
     if ((st = upload(m, s.off, (size_t)(d.ns + 1) * 4, &p))) return fail(st);
     d.off = (const int *)p;
     if ((st = upload(m, s.idx, (size_t)L * 4, &p))) return fail(st);
@@ -607,6 +623,7 @@ extern "C" int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **ou
         d.At = (const float *)p;
     }
     if ((st = model_fill_param(m, s.x0_s, s.phi_c, s.x0_c, s.gamma_c))) return fail(st);
+    if ((st = model_fill_inflow(m, s.u_s))) return fail(st);
     *out = m;
     return PTROM_OK;
 }
@@ -621,6 +638,11 @@ extern "C" int ptrom_set_param(ptrom_model *m, const double *x0_s, const double 
                                const double *gamma_c) {
     if (!m) return set_error(PTROM_EINVAL, "ptrom_set_param: NULL model");
     return model_fill_param(m, x0_s, phi_c, x0_c, gamma_c);
+}
+
+extern "C" int ptrom_set_inflow(ptrom_model *m, const double *u_s) {
+    if (!m) return set_error(PTROM_EINVAL, "ptrom_set_inflow: NULL model");
+    return model_fill_inflow(m, u_s);
 }
 
 extern "C" size_t ptrom_state_bytes(const ptrom_model *m) {

@@ -200,6 +200,7 @@ struct T2 {
     const float *x0c;   // [2Nc]
     const float *gc;    // [Nc]
     const int *off, *idx;
+    const float *u;     // [2n]       dt times the superimposed inflow (Sec. 6.3), zeros for none
 };
 
 // rows < 2n: xt = x0 + Phi xh and pd = Phi dxh; rows >= 2n: xq = x0c + Phic xh
@@ -260,8 +261,8 @@ __global__ void k_t2_pairs(T2 t, const float *xt, const float *xq, const float *
         D[i] = d00;
         D[t.n + i] = d01;
         D[2 * t.n + i] = -d10n;
-        const float r0 = pd[i] - t.h * (-u + fprev[i]);
-        const float r1 = pd[t.n + i] - t.h * (v + fprev[t.n + i]);
+        const float r0 = pd[i] - t.h * (-u + fprev[i]) - t.u[i];
+        const float r1 = pd[t.n + i] - t.h * (v + fprev[t.n + i]) - t.u[t.n + i];
         r[i] = r0;
         r[t.n + i] = r1;
         if (rcol) {
@@ -868,10 +869,12 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_TRY(scratch_alloc(&work, wbytes, st));
     for (int q = 0; q < n_params; ++q) {
         const double *x0 = x0s + (size_t)q * nd, *G = gammas + (size_t)q * n;
+        ptrom_fom_params fq = p->fom;
+        fq.u_inf = p->u_infs ? p->u_infs + (size_t)q * nd : nullptr;
         PTROM_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * nd, cudaMemcpyDeviceToDevice, st));
         PTROM_TRY(velocity(n, x, n, x, G, delta, f, nullptr, p->fom.prec, st));
         for (int s = 0; s < p->steps; ++s) {
-            const int stt = fom_step(&p->fom, n, G, x, f, work, wbytes, nullptr, stream);
+            const int stt = fom_step(&fq, n, G, x, f, work, wbytes, nullptr, stream);
             if (stt != PTROM_OK && stt != PTROM_ENOCONV) return stt;
             k_snapshot<<<(nd + 255) / 256, 256, 0, st>>>(nd, x, S + (size_t)(q * p->steps + s) * nd);
             count_launch();
@@ -973,7 +976,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     const long long want_res = (long long)n_params * p->steps * std::min(std::max(p->max_gn, 1), 10);
     const int maxres = (int)std::min<long long>(std::min<long long>(want_res, 262144), (long long)(24e9 / (8.0 * nd)));
     // device buffers for Tier II
-    float *dphi, *dx0, *dphic, *dx0c, *dgc, *dxt, *dpd, *dxq, *dxh, *ddx, *df, *dfp, *dD, *dr, *dpart;
+    float *dphi, *dx0, *dphic, *dx0c, *dgc, *dxt, *dpd, *dxq, *dxh, *ddx, *df, *dfp, *dD, *dr, *dpart, *du;
     int *doff, *didx;
     double *dout, *R;
     auto falloc = [&](float **pp, size_t cnt) { return scratch_alloc((void **)pp, sizeof(float) * std::max<size_t>(cnt, 4), st); };
@@ -992,6 +995,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_TRY(falloc(&dD, 3 * (size_t)n));
     PTROM_TRY(falloc(&dr, nd));
     PTROM_TRY(falloc(&dpart, (size_t)nblk * nout));
+    PTROM_TRY(falloc(&du, nd));
     PTROM_TRY(scratch_alloc((void **)&doff, sizeof(int) * (n + 1), st));
     PTROM_TRY(scratch_alloc((void **)&didx, sizeof(int) * std::max<size_t>(all.idx.size(), 1), st));
     PTROM_TRY(scratch_alloc((void **)&dout, sizeof(double) * nout, st));
@@ -1000,7 +1004,9 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_CUDA(cudaMemcpyAsync(doff, all.off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
     if (!all.idx.empty())
         PTROM_CUDA(cudaMemcpyAsync(didx, all.idx.data(), sizeof(int) * all.idx.size(), cudaMemcpyHostToDevice, st));
-    T2 t2{n, NcA, M, Mp, (float)(0.5 * dt), (float)delta, dphi, dx0, dphic, dx0c, dgc, doff, didx};
+    T2 t2{n, NcA, M, Mp, (float)(0.5 * dt), (float)delta, dphi, dx0, dphic, dx0c, dgc, doff, didx, du};
+    std::vector<double> uq(nd, 0.0), u_first(nd, 0.0);
+    std::vector<float> uf(nd, 0.f);
     const int gth = 256;
     const int grows = (nd + 2 * NcA + gth - 1) / gth;
     const int gpair = (n * 32 + gth - 1) / gth;
@@ -1033,6 +1039,13 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
             x0cQ[NcA + c] = xc[1];
         }
     }
+    if (p->u_infs) {
+        PTROM_CUDA(cudaMemcpyAsync(uq.data(), p->u_infs + (size_t)q * nd, sizeof(double) * nd, cudaMemcpyDeviceToHost, st));
+        PTROM_CUDA(cudaStreamSynchronize(st));
+        if (q == 0) u_first = uq;
+    }
+    for (int d = 0; d < nd; ++d) uf[d] = (float)(dt * uq[d]);
+    PTROM_CUDA(cudaMemcpyAsync(du, uf.data(), sizeof(float) * nd, cudaMemcpyHostToDevice, st));
     for (int d = 0; d < nd; ++d) x0f[d] = (float)(xq[d] - (d < n ? ox : oy));
     for (int rr = 0; rr < 2 * NcA; ++rr) {
         for (int m = 0; m < M; ++m) phicf[(size_t)rr * Mp + m] = (float)phicQ[(size_t)rr * M + m];
@@ -1164,7 +1177,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     inf.seconds_sample = secs(t0);
     // free the stage buffers
     for (void *b : std::vector<void *>{S, x, f, work, dphi, dx0, dphic, dx0c, dgc, dxt, dpd, dxq, dxh, ddx, df, dfp, dD,
-                                        dr, dpart, doff, didx, dout, R})
+                                        dr, dpart, du, doff, didx, dout, R})
         PTROM_TRY(scratch_free(b, st));
     PTROM_CUDA(cudaStreamSynchronize(st));
     PTROM_TRY(scratch_trim());  // hand the training buffers back to the device
@@ -1187,6 +1200,12 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     desc.A = Ah.data();
     desc.off = off.data();
     desc.idx = idx.empty() ? off.data() : idx.data();
+    std::vector<double> u_s(2 * (size_t)ns);
+    for (int s = 0; s < ns; ++s) {
+        u_s[s] = u_first[sampled[s]];
+        u_s[ns + s] = u_first[n + sampled[s]];
+    }
+    desc.u_s = p->u_infs ? u_s.data() : nullptr;
     ptrom_model *m = nullptr;
     PTROM_TRY(ptrom_model_create(&desc, &m));
     m->built = true;
@@ -1255,6 +1274,21 @@ extern "C" int ptrom_set_param_full(ptrom_model *m, const double *x0, const doub
     PTROM_CUDA(cudaMemcpyAsync(m->x0_dev, x0, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, st));
     m->x0_full = xh;
     return PTROM_OK;
+}
+
+extern "C" int ptrom_set_inflow_full(ptrom_model *m, const double *u, ptrom_stream_t stream) {
+    if (!m || !m->built) return set_error(PTROM_EINVAL, "ptrom_set_inflow_full: model not made by ptrom_build");
+    if (!u) return ptrom_set_inflow(m, nullptr);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = m->n, ns = m->d.ns;
+    std::vector<double> uh(2 * (size_t)n), u_s(2 * (size_t)ns);
+    PTROM_CUDA(cudaMemcpyAsync(uh.data(), u, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
+    PTROM_CUDA(cudaStreamSynchronize(st));
+    for (int s = 0; s < ns; ++s) {
+        u_s[s] = uh[m->sampled[s]];
+        u_s[ns + s] = uh[n + m->sampled[s]];
+    }
+    return ptrom_set_inflow(m, u_s.data());
 }
 
 extern "C" int ptrom_reconstruct(const ptrom_model *m, const double *xhat, const int *rows, int nrows, double *out,

@@ -4,13 +4,15 @@
 //
 // File layout (native little-endian; both supported hosts are):
 //   char[8]  "PTROMMDL"
-//   u32      0x01020304 (byte-order check), u32 format version (1)
+//   u32      0x01020304 (byte-order check), u32 format version (2; 1 is
+//            still read: it has no inflow array)
 //   i32 x 8  n_s, M, M_r, N_c, max_gn, qr_prec, built, n
 //   f64 x 5  dt, delta, tol, and the origin (ox, oy) the model's FP32
 //            coordinates are taken relative to (fixed when the model was
 //            created, kept across reparametrisations)
 //   arrays, each as u64 element count then the elements:
 //     f64 phi_s, x0_s, phi_c, x0_c, gamma_c, A;   i32 off, idx
+//     f64 u_s (version 2: the superimposed inflow, 0 or 2 n_s elements)
 //   built models only:
 //     f64 phi, sigma;  i32 sampled, cl_off, cl_mem;  f64 x0
 //   u64      FNV-1a hash of every preceding byte
@@ -27,7 +29,7 @@ namespace ptrom {
 namespace {
 
 constexpr char kMagic[8] = {'P', 'T', 'R', 'O', 'M', 'M', 'D', 'L'};
-constexpr unsigned kOrder = 0x01020304u, kVersion = 1u;
+constexpr unsigned kOrder = 0x01020304u, kVersion = 2u;
 
 struct Writer {
     std::vector<unsigned char> buf;
@@ -102,6 +104,7 @@ extern "C" int ptrom_save(const ptrom_model *m, const char *path) {
     w.arr(m->h_A);
     w.arr(m->h_off);
     w.arr(m->h_idx);
+    w.arr(m->h_u_s);
     if (m->built) {
         w.arr(m->phi);
         w.arr(m->sigma);
@@ -140,7 +143,8 @@ extern "C" int ptrom_load(const char *path, ptrom_model **out) {
     if (!r.ok || memcmp(magic, kMagic, 8) != 0) return set_error(PTROM_EINVAL, "ptrom_load: '%s' is not a model", path);
     if (r.val<unsigned>() != kOrder) return set_error(PTROM_EINVAL, "ptrom_load: byte order differs");
     const unsigned ver = r.val<unsigned>();
-    if (ver != kVersion) return set_error(PTROM_EINVAL, "ptrom_load: format version %u, expected %u", ver, kVersion);
+    if (ver != kVersion && ver != 1u)
+        return set_error(PTROM_EINVAL, "ptrom_load: format version %u, expected 1 or %u", ver, kVersion);
     const int ns = r.val<int>(), M = r.val<int>(), Mr = r.val<int>(), Nc = r.val<int>();
     const int max_gn = r.val<int>(), qr_prec = r.val<int>(), built = r.val<int>(), n = r.val<int>();
     const double dt = r.val<double>(), delta = r.val<double>(), tol = r.val<double>();
@@ -154,6 +158,13 @@ extern "C" int ptrom_load(const char *path, ptrom_model **out) {
     const auto off = r.arr<int>(ns + 1);
     const size_t L = (r.ok && off.size() == (size_t)ns + 1 && off[ns] >= 0) ? (size_t)off[ns] : 0;
     const auto idx = r.arr<int>(L);
+    std::vector<double> u_s;
+    if (ver >= 2u) {  // the inflow array: empty or one value per sampled dof
+        const size_t at = r.at;
+        const unsigned long long len = r.val<unsigned long long>();
+        r.at = at;
+        u_s = r.arr<double>(len == 0 ? 0 : 2 * (size_t)ns);
+    }
     if (!r.ok) return set_error(PTROM_EINVAL, "ptrom_load: truncated or inconsistent arrays");
     std::vector<double> phi, sigma, x0;
     std::vector<int> sampled, cl_off, cl_mem;
@@ -192,6 +203,7 @@ extern "C" int ptrom_load(const char *path, ptrom_model **out) {
     desc.A = A.data();
     desc.off = off.data();
     desc.idx = idx.empty() ? off.data() : idx.data();
+    desc.u_s = u_s.empty() ? nullptr : u_s.data();
     ptrom_model *m = nullptr;
     PTROM_TRY(ptrom_model_create(&desc, &m));
     if (m->ox != ox || m->oy != oy) {  // the saved origin, then the FP32 arrays again

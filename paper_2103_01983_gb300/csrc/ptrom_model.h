@@ -21,6 +21,7 @@ struct DevModel {
     const float *phiT;  // [2Nc][Mp]
     const float *x0T;   // [2Nc]   relative to origin
     const float *gT;    // [Nc]    Gamma~ / (2 pi)
+    const float *uB;    // [2ns]   dt times the superimposed inflow at the sampled dofs (zeros: none)
     const int *off, *idx;
     const float *At;    // [2ns][Mrp]  (A transposed, zero padded)
     int nlist;          // off[ns]: cluster-list entries
@@ -46,6 +47,7 @@ struct ptrom_model {
     // host FP64 copies of the description (kept for ptrom_save)
     int qr_prec = 0;
     std::vector<double> h_phi_s, h_x0_s, h_phi_c, h_x0_c, h_gamma_c, h_A;
+    std::vector<double> h_u_s;  // [2 n_s] superimposed inflow at the sampled dofs (empty: none)
     std::vector<int> h_off, h_idx;
     // offline data, kept by models made with ptrom_build
     bool built = false;
@@ -65,6 +67,9 @@ namespace ptrom {
 // Fill the parameter-dependent device arrays of a model from host arrays.
 int model_fill_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
                      const double *gamma_c);
+// Set the superimposed inflow at the sampled dofs (host [2 n_s]; nullptr
+// clears it).
+int model_fill_inflow(ptrom_model *m, const double *u_s);
 // Give a built model its FP64 basis and reference state on the device
 // (reconstruction); phi [2n][M] row-major, x0 [2n], host arrays.
 int model_store_basis(ptrom_model *m, const double *phi, const double *x0);

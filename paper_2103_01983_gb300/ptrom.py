@@ -46,7 +46,7 @@ class FomParams(ctypes.Structure):
     """Mirror of ptrom_fom_params."""
     _fields_ = [("dt", _d), ("delta", _d), ("tol", _d), ("max_iter", _i), ("jac_mode", _i),
                 ("p_it", _i), ("prec", _i), ("gmres_restart", _i), ("gmres_max_iter", _i),
-                ("gmres_rtol", _d)]
+                ("gmres_rtol", _d), ("u_inf", _vp)]
 
 
 class FomStats(ctypes.Structure):
@@ -79,7 +79,7 @@ class ModelDesc(ctypes.Structure):
     _fields_ = [("n_s", _i), ("M", _i), ("M_r", _i), ("N_c", _i), ("dt", _d), ("delta", _d),
                 ("tol", _d), ("max_gn", _i), ("qr_prec", _i),
                 ("phi_s", _vp), ("x0_s", _vp), ("phi_c", _vp), ("x0_c", _vp), ("gamma_c", _vp),
-                ("A", _vp), ("off", _vp), ("idx", _vp)]
+                ("A", _vp), ("off", _vp), ("idx", _vp), ("u_s", _vp)]
 
 
 class PtromStats(ctypes.Structure):
@@ -90,7 +90,8 @@ class PtromStats(ctypes.Structure):
 class BuildParams(ctypes.Structure):
     """Mirror of ptrom_build_params."""
     _fields_ = [("M", _i), ("M_r", _i), ("n_s", _i), ("criterion", _i), ("theta", _d), ("p_c", _d),
-                ("steps", _i), ("tol", _d), ("max_gn", _i), ("qr_prec", _i), ("fom", FomParams)]
+                ("steps", _i), ("tol", _d), ("max_gn", _i), ("qr_prec", _i), ("fom", FomParams),
+                ("u_infs", _vp)]
 
 
 class BuildInfo(ctypes.Structure):
@@ -120,6 +121,8 @@ def _load():
         "ptrom_model_create": ([ctypes.POINTER(ModelDesc), ctypes.POINTER(_vp)], _i),
         "ptrom_free": ([_vp], None),
         "ptrom_set_param": ([_vp, _vp, _vp, _vp, _vp], _i),
+        "ptrom_set_inflow": ([_vp, _vp], _i),
+        "ptrom_set_inflow_full": ([_vp, _vp, _vp], _i),
         "ptrom_state_bytes": ([_vp], ctypes.c_size_t),
         "ptrom_step": ([ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                         ctypes.POINTER(_vp), _i, ctypes.POINTER(PtromStats), _vp], _i),
@@ -290,9 +293,21 @@ def fom_workspace(params, n, device="cuda"):
     return torch.empty(int(nbytes), dtype=torch.uint8, device=device)
 
 
-def fom_step(params, Gamma, x, f, work=None, stream=None, allow_noconv=False):
-    """One implicit trapezoid step in place on (x, f).  Returns the stats dict."""
+def _with_inflow(params, u_inf):
+    """A copy of params whose u_inf is the device tensor u_inf [2n] (or none)."""
+    if u_inf is None:
+        return params
+    q = FomParams.from_buffer_copy(params)
+    q.u_inf = _ptr(u_inf).value
+    return q
+
+
+def fom_step(params, Gamma, x, f, work=None, stream=None, allow_noconv=False, u_inf=None):
+    """One implicit trapezoid step in place on (x, f).  Returns the stats dict.
+    u_inf: optional device tensor [2n], the superimposed inflow velocity
+    (f stays the pair sum)."""
     n = Gamma.numel()
+    params = _with_inflow(params, u_inf)
     if work is None:
         work = fom_workspace(params, n, x.device)
     st = FomStats()
@@ -323,17 +338,19 @@ class PtromModel:
     gamma_c (N_c), A (M_r, 2 n_s), CSR lists off (n_s+1) / idx."""
 
     def __init__(self, phi_s, x0_s, phi_c, x0_c, gamma_c, A, off, idx, dt, delta, tol=1e-4,
-                 max_gn=100, qr_prec="fp64"):
+                 max_gn=100, qr_prec="fp64", u_s=None):
         import numpy as np
         keep = [_host(phi_s, np.float64), _host(x0_s, np.float64), _host(phi_c, np.float64),
                 _host(x0_c, np.float64), _host(gamma_c, np.float64), _host(A, np.float64),
                 _host(off, np.int32), _host(idx, np.int32)]
+        us = None if u_s is None else _host(u_s, np.float64)
         ns = keep[1].size // 2
         M = keep[0].shape[1]
         Mr = keep[5].shape[0]
         Nc = keep[4].size
         d = ModelDesc(ns, M, Mr, Nc, float(dt), float(delta), float(tol), int(max_gn), _prec(qr_prec),
-                      *[ctypes.c_void_p(a.ctypes.data) for a in keep])
+                      *[ctypes.c_void_p(a.ctypes.data) for a in keep],
+                      None if us is None else ctypes.c_void_p(us.ctypes.data))
         h = ctypes.c_void_p()
         _check(lib.ptrom_model_create(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -369,6 +386,16 @@ class PtromModel:
     def set_param_full(self, x0, Gamma, stream=None):
         """Reload the clusters for a new parameter (device x0 [2n], Gamma [n])."""
         _check(lib.ptrom_set_param_full(self.handle, _ptr(x0), _ptr(Gamma), _stream(stream)))
+
+    def set_inflow(self, u_s=None):
+        """Superimposed inflow at the sampled dofs (host [2 n_s]; None removes it)."""
+        import numpy as np
+        us = None if u_s is None else _host(u_s, np.float64)
+        _check(lib.ptrom_set_inflow(self.handle, None if us is None else ctypes.c_void_p(us.ctypes.data)))
+
+    def set_inflow_full(self, u=None, stream=None):
+        """Superimposed inflow from the full per-body array (device [2n]; None removes it)."""
+        _check(lib.ptrom_set_inflow_full(self.handle, None if u is None else _ptr(u), _stream(stream)))
 
     def reconstruct(self, xhat, rows=None, stream=None):
         """x = x^0 + Phi xhat on the listed bodies (default all) -> [chi..., psi...]."""
@@ -420,14 +447,20 @@ CRITERIA = {"bh": 0, "barnes_hut": 0, "nb": 1, "neighbor": 1}
 
 
 def ptrom_build(x0s, gammas, M, M_r, n_s, steps, fom, criterion="bh", theta=0.5, p_c=1.0, tol=1e-4,
-                max_gn=100, qr_prec="fp64", stream=None):
-    """Offline training (Stages 1-4) from device tensors x0s [P, 2n], gammas [P, n].
+                max_gn=100, qr_prec="fp64", stream=None, u_infs=None):
+    """Offline training (Stages 1-4) from device tensors x0s [P, 2n], gammas [P, n]
+    and optionally u_infs [P, 2n] (superimposed inflow per parameter).
     Returns (PtromModel, info dict)."""
     x0s = x0s.contiguous()
     gammas = gammas.contiguous()
     P, n = gammas.shape
+    if u_infs is not None:
+        u_infs = u_infs.contiguous()
+        if u_infs.shape != x0s.shape or u_infs.device != x0s.device:
+            raise ValueError("u_infs must be shaped like x0s, on its device")
     bp = BuildParams(int(M), int(M_r), int(n_s), CRITERIA[criterion], float(theta), float(p_c), int(steps),
-                     float(tol), int(max_gn), _prec(qr_prec), fom)
+                     float(tol), int(max_gn), _prec(qr_prec), fom,
+                     _ptr(u_infs))
     h = ctypes.c_void_p()
     info = BuildInfo()
     _check(lib.ptrom_build(ctypes.byref(bp), int(n), int(P), _ptr(x0s), _ptr(gammas), ctypes.byref(h),

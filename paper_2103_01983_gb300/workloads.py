@@ -153,6 +153,42 @@ def vortex_pair_params(seed: int = 0):
 
 
 # --------------------------------------------------------------- the paper's
+# mushroom-cloud experiment (Sec. 6.3): N bodies evenly spaced on the line
+# psi = -10 from chi = -37.43 to 37.43 (spacing 0.15); end circulations
+# mu = (Gamma_1, Gamma_N) in [-1, -0.5] x [0.5, 1] x Gamma_max (Gamma_max =
+# 220, opposite senses), every other body 0.01; delta = 0.15 (the initial
+# spacing, taken as the additive constant as for the vortex pair), dt =
+# 0.005, t in [0, 5].  Every body also carries a constant inflow velocity
+# (0, 5 sqrt(1.125^2 - s_i^2) + 0.5), s_i = linspace(-1, 1, N)_i: a
+# semicircular profile over the body index.
+MUSHROOM = {"n": 500, "half_width": 37.43, "psi0": -10.0, "gamma_max": 220.0, "gamma_weak": 0.01,
+            "delta": 0.15, "dt": 0.005, "steps": 1000, "lo": 0.5}
+
+
+def mushroom(g1: float, gN: float, n: int = MUSHROOM["n"]):
+    """State [chi..., psi...], circulations and inflow [u_chi..., u_psi...]
+    of the mushroom-cloud experiment."""
+    s = np.linspace(-MUSHROOM["half_width"], MUSHROOM["half_width"], n)
+    x = np.concatenate([s, np.full(n, MUSHROOM["psi0"])])
+    G = np.full(n, MUSHROOM["gamma_weak"])
+    G[0], G[-1] = g1, gN
+    c = np.linspace(-1.0, 1.0, n)
+    u = np.concatenate([np.zeros(n), 5.0 * np.sqrt(1.125 ** 2 - c * c) + 0.5])
+    return x, G, u
+
+
+def mushroom_params(seed: int = 0):
+    """Training mu (4 Latin-hypercube points) and the 6 x 6 query grid over
+    [-1, -lo] x [lo, 1] x Gamma_max (Sec. 6.3)."""
+    lo, gmax = MUSHROOM["lo"], MUSHROOM["gamma_max"]
+    unit = param_lhs(4, seed, (0.0, 1.0), (0.0, 1.0))
+    train = np.stack([-gmax + unit[:, 0] * (1.0 - lo) * gmax, lo * gmax + unit[:, 1] * (1.0 - lo) * gmax], axis=1)
+    ga, gb = np.linspace(-gmax, -lo * gmax, 6), np.linspace(lo * gmax, gmax, 6)
+    query = np.array([(a, b) for a in ga for b in gb])
+    return train, query
+
+
+# --------------------------------------------------------------- the paper's
 # single-vortex reproductive experiment (Sec. 6.4, Table 1): N bodies on the
 # line linspace(-N, N, N) in both coordinates, delta = 0, every body 0.01
 # except the centre body (index N // 2), which carries Gamma_center; dt and

@@ -9,20 +9,20 @@ from oracle import fom, rom
 
 
 def build_case(x0, G, delta, dt, steps, M, n_s, M_r, criterion="bh", theta=0.5, p_c=1.0,
-               tol=1e-4, fom_mode="dense"):
+               tol=1e-4, fom_mode="dense", u_inf=None):
     N = G.size
-    traj, _ = fom.rollout(x0, G, delta, dt, steps, mode=fom_mode, tol=1e-12)
+    traj, _ = fom.rollout(x0, G, delta, dt, steps, mode=fom_mode, tol=1e-12, u_inf=u_inf)
     S = traj[1:].T                                              # R1: the states x^1..x^Nt
     Phi, sig = rom.pod(S, M)
     cl_all, _ = rom.cluster_tables(Phi, sig, x0, G, np.arange(N), criterion=criterion,
                                    theta=theta, p_c=p_c)
-    _, snaps = rom.lspg_tier2(cl_all, Phi, x0, delta, dt, steps, tol=tol)
+    _, snaps = rom.lspg_tier2(cl_all, Phi, x0, delta, dt, steps, tol=tol, u_inf=u_inf)
     Phi_r, _ = rom.pod(snaps, M_r)
     sampled = rom.greedy_sample(Phi_r, n_s, N)
     A = rom.gappy_operator(Phi_r, sampled, N)
     cl, _ = rom.cluster_tables(Phi, sig, x0, G, sampled, criterion=criterion, theta=theta, p_c=p_c)
     return dict(traj=traj, Phi=Phi, sig=sig, cl=cl, A=A, sampled=sampled, x0=x0, G=G,
-                delta=delta, dt=dt)
+                delta=delta, dt=dt, u=u_inf)
 
 
 def model_arrays(case):
@@ -32,5 +32,7 @@ def model_arrays(case):
     off = np.zeros(len(cl.lists) + 1, dtype=np.int32)
     off[1:] = np.cumsum([len(li) for li in cl.lists])
     idx = np.concatenate([np.asarray(li, dtype=np.int32) for li in cl.lists]) if off[-1] else np.zeros(0, np.int32)
+    u = case.get("u")
+    u_s = None if u is None else rom.target_rows(np.asarray(u)[:, None], x0, cl.targets)[0][:, 0]
     return dict(phi_s=Phi_t, x0_s=x0_t, phi_c=cl.Phit, x0_c=cl.x0t, gamma_c=cl.Gt, A=case["A"],
-                off=off, idx=idx)
+                off=off, idx=idx, u_s=u_s)

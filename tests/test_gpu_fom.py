@@ -185,3 +185,58 @@ def test_fp32_krylov_matches_fp64_krylov(P):
     assert all(s["converged"] and s["res_norm"] <= 1e-8 * xnorm for s in sa + sb)
     # each end state is within a Newton-tolerance-sized ball of the other
     assert np.linalg.norm(ta[-1] - tb[-1]) <= 1e-6 * xnorm
+
+
+def _gpu_rollout_inflow(P, x0, G, u, params, steps, prec):
+    x = _dev(x0)
+    Gt = _dev(G)
+    ut = _dev(u)
+    f = P.bs_velocity(x, Gt, params.delta, prec=prec)
+    work = P.fom_workspace(params, G.size)
+    traj = [x0.copy()]
+    for _ in range(steps):
+        assert P.fom_step(params, Gt, x, f, work=work, u_inf=ut)["converged"]
+        traj.append(x.cpu().numpy())
+    return np.array(traj), f.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["blockdiag", "jfnk", "dense"])
+def test_inflow_fp64_against_oracle(P, mode):
+    """Superimposed inflow (Sec. 6.3) on a non-uniform profile: every Newton
+    variant matches the FP64 oracle, and f stays the pair sum."""
+    x0, G = W.disk(300, seed=3)
+    c = np.linspace(-1.0, 1.0, 300)
+    u = np.concatenate([0.4 * np.sin(3.0 * c), 5.0 * np.sqrt(1.125 ** 2 - c * c) + 0.5])
+    params = P.fom_params(0.01, 0.05, mode, tol=1e-13, prec="fp64", gmres_rtol=1e-10)
+    traj, f = _gpu_rollout_inflow(P, x0, G, u, params, 4, "fp64")
+    ref, _ = fom.rollout(x0, G, 0.05, 0.01, 4, mode="dense", tol=1e-14, u_inf=u)
+    assert np.abs(traj - ref).max() <= 1e-11
+    np.testing.assert_allclose(f, direct.velocity(traj[-1], G, 0.05), atol=1e-11)
+
+
+def test_mushroom_fom_fp32c_against_oracle(P):
+    """The mushroom-cloud workload (Sec. 6.3, N = 500, Gamma_max ends, the
+    semicircular inflow), 40 steps of JFNK with FP32 pair sums against the
+    FP64 dense oracle; Gamma = 0 moves every body by dt u per step."""
+    x0, G, u = W.mushroom(-220.0, 220.0)
+    M = W.MUSHROOM
+    params = P.fom_params(M["dt"], M["delta"], "jfnk", prec="fp32c")
+    traj, _ = _gpu_rollout_inflow(P, x0, G, u, params, 40, "fp32c")
+    ref, _ = fom.rollout(x0, G, M["delta"], M["dt"], 40, mode="dense", tol=1e-13, u_inf=u)
+    disp = np.abs(ref - x0).max()
+    assert np.abs(traj - ref).max() <= 1e-5 * disp
+    params64 = P.fom_params(M["dt"], M["delta"], "blockdiag", tol=1e-13, prec="fp64")
+    still, _ = _gpu_rollout_inflow(P, x0, np.zeros(500), u, params64, 3, "fp64")
+    np.testing.assert_allclose(still, x0 + np.arange(4)[:, None] * M["dt"] * u, rtol=0, atol=1e-12)
+
+
+def test_batched_fom_rejects_inflow(P):
+    from paper_2103_01983_gb300.ptrom import PtromError
+    x0, G = W.disk(64, seed=1)
+    params = P.fom_params(0.01, 0.05, "blockdiag", prec="fp64")
+    ut = _dev(np.ones(128))
+    q = P._with_inflow(params, ut)
+    x, Gt = _dev(x0), _dev(G)
+    f = P.bs_velocity(x, Gt, 0.05, prec="fp64")
+    with pytest.raises(PtromError):
+        P.fom_step_batched(q, [Gt], [x], [f], [P.fom_workspace(params, 64)])

@@ -27,7 +27,13 @@ _CASES = {}
 
 def _case(name):
     if name not in _CASES:
-        if name.startswith("disk"):
+        if name == "mushroom_bh":
+            # the mushroom-cloud workload (Sec. 6.3) at 200 bodies: opposite
+            # end vortices and the semicircular superimposed inflow
+            x0, G, u = W.mushroom(-200.0, 150.0, n=200)
+            _CASES[name] = build_case(x0, G, 0.15, 0.005, 100, M=16, n_s=40, M_r=32, criterion="nb",
+                                      p_c=1.0, u_inf=u)
+        elif name.startswith("disk"):
             x0, G = W.disk(256, seed=0)
             th = 0.0 if name == "disk_gnat" else 0.5
             _CASES[name] = build_case(x0, G, 0.05, 0.01, 100, M=8, n_s=32, M_r=16, theta=th)
@@ -41,7 +47,7 @@ def _case(name):
 def _model(P, case, **kw):
     arr = model_arrays(case)
     return P.PtromModel(arr["phi_s"], arr["x0_s"], arr["phi_c"], arr["x0_c"], arr["gamma_c"], arr["A"],
-                        arr["off"], arr["idx"], case["dt"], case["delta"], **kw)
+                        arr["off"], arr["idx"], case["dt"], case["delta"], u_s=arr["u_s"], **kw)
 
 
 @pytest.fixture(scope="module")
@@ -50,7 +56,7 @@ def P():
     return ptrom
 
 
-@pytest.fixture(scope="module", params=["disk_gnat", "disk_bh", "pair_gnat"])
+@pytest.fixture(scope="module", params=["disk_gnat", "disk_bh", "pair_gnat", "mushroom_bh"])
 def case(request):
     return _case(request.param)
 
@@ -59,7 +65,7 @@ def case(request):
 def test_one_gauss_newton_update(P, case, qr):
     M = case["Phi"].shape[1]
     ref, _ = rom.ptrom_online(case["cl"], case["Phi"], case["x0"], case["A"], case["delta"], case["dt"],
-                              1, tol=1e-4, max_gn=1)
+                              1, tol=1e-4, max_gn=1, u_inf=case.get("u"))
     m = _model(P, case, tol=1e-4, max_gn=1, qr_prec=qr)
     st = m.new_state()
     xh = torch.zeros(M, dtype=torch.float64, device="cuda")
@@ -88,7 +94,7 @@ def _qoi_gap(case, xa, xb):
 def test_trajectory_matches_oracle_qoi(P, case, qr):
     M = case["Phi"].shape[1]
     ref, it_ref = rom.ptrom_online(case["cl"], case["Phi"], case["x0"], case["A"], case["delta"],
-                                   case["dt"], 100, tol=1e-4)
+                                   case["dt"], 100, tol=1e-4, u_inf=case.get("u"))
     m = _model(P, case, tol=1e-4, qr_prec=qr)
     st = m.new_state()
     hist = torch.zeros(100, M, dtype=torch.float64, device="cuda")

@@ -244,3 +244,30 @@ def test_tier2_collects_residuals_of_every_training_parameter(P):
         errs.append(np.abs(rec - np.array(ref)).max() / disp)
     print("relative errors", errs)
     assert max(errs) <= 1e-5, errs
+
+
+def test_inflow_model_save_load_and_clear(P, tmp_path):
+    """The superimposed inflow is part of a built model: it survives
+    ptrom_save / ptrom_load, and set_inflow(None) returns the model to the
+    no-inflow trajectory."""
+    x0, G, u = W.mushroom(-150.0, 150.0, n=128)
+    fp = P.fom_params(0.005, 0.15, "jfnk", prec="fp32c")
+    model, _ = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 12, 24, 24, 40, fp, criterion="nb", p_c=1.0,
+                             u_infs=_dev(u)[None])
+
+    def run(m):
+        st = m.new_state()
+        xh = torch.zeros(12, dtype=torch.float64, device="cuda")
+        P.ptrom_step([m], [st], 40, xhat=[xh])
+        return xh.cpu().numpy()
+
+    a = run(model)
+    path = tmp_path / "inflow.ptrom"
+    model.save(path)
+    b = run(P.PtromModel.load(path))
+    np.testing.assert_array_equal(a, b)
+    model.set_inflow(None)
+    c = run(model)
+    assert np.abs(c - a).max() > 1e-3 * np.abs(a).max()
+    model.set_inflow_full(_dev(u))
+    np.testing.assert_array_equal(run(model), a)

@@ -79,3 +79,43 @@ def test_adjoint_matches_finite_differences():
         Lm = lam_T @ fom.rollout(x0 - h * dx, G - h * dg, 0.05, 0.01, 6, mode="dense", tol=1e-14)[0][-1]
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - (gx @ dx + gG @ dg)) <= 1e-7 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("mode", ["dense", "blockdiag", "jfnk"])
+def test_inflow_without_circulation_is_uniform_motion(mode):
+    """Gamma = 0 leaves only the superimposed inflow (Sec. 6.3): every body
+    moves by dt u per step, exactly."""
+    x, _, u = W.mushroom(-100.0, 100.0, n=16)
+    G = np.zeros(16)
+    traj, it = fom.rollout(x, G, 0.15, 0.005, 6, mode=mode, tol=1e-14, u_inf=u)
+    k = np.arange(7)[:, None]
+    np.testing.assert_allclose(traj, x + k * 0.005 * u, rtol=0, atol=1e-12)
+
+
+def test_uniform_inflow_is_a_galilean_shift():
+    """Pair sums depend on differences only, so a uniform inflow U moves the
+    whole no-inflow trajectory by n dt U (Newton tolerance)."""
+    x, G = W.disk(48, seed=5)
+    delta, dt, steps = 0.05, 0.01, 8
+    U = np.concatenate([np.full(48, 0.7), np.full(48, -1.3)])
+    ref, _ = fom.rollout(x, G, delta, dt, steps, mode="dense", tol=1e-14)
+    got, _ = fom.rollout(x, G, delta, dt, steps, mode="dense", tol=1e-14, u_inf=U)
+    k = np.arange(steps + 1)[:, None]
+    np.testing.assert_allclose(got, ref + k * dt * U, rtol=0, atol=1e-11)
+
+
+def test_mushroom_workload_matches_the_paper():
+    """Sec. 6.3: end bodies at (-37.43, -10) and (37.43, -10), spacing 0.15,
+    the inflow peak 5 * 1.125 + 0.5 at the middle and 5 sqrt(1.125^2 - 1) + 0.5
+    at the ends."""
+    x, G, u = W.mushroom(-220.0, 110.0)
+    n = 500
+    assert (x[0], x[n - 1], x[n], x[2 * n - 1]) == (-37.43, 37.43, -10.0, -10.0)
+    assert np.diff(x[:n]) == pytest.approx(0.15, abs=2e-4)
+    assert (G[0], G[-1], G[1]) == (-220.0, 110.0, 0.01)
+    assert np.all(u[:n] == 0.0)
+    assert u[n] == pytest.approx(5 * np.sqrt(1.125 ** 2 - 1) + 0.5, rel=1e-15)
+    assert u[n:].max() == pytest.approx(5 * 1.125 + 0.5, rel=1e-5)
+    train, query = W.mushroom_params(0)
+    assert train.shape == (4, 2) and query.shape == (36, 2)
+    assert np.all((train[:, 0] >= -220) & (train[:, 0] <= -110) & (train[:, 1] >= 110) & (train[:, 1] <= 220))
