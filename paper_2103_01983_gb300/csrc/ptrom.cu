@@ -66,7 +66,9 @@ __host__ __device__ inline SmemLayout smem_layout(int ns, int M, int Mr, int Nc,
     L.D = take(4 * 3 * (size_t)ns);
     L.xq = take(4 * 2 * (size_t)Nc);
     L.gq = take(4 * (size_t)Nc);
-    L.Bf = take(4 * (size_t)Mrp * (M + 1));                    // column-major, ld = Mrp, column M = rhs
+    // [A C | A r], column-major, ld = Mrp, column M = rhs: FP64 for the FP64
+    // QR (assembled in place), else FP32
+    L.Bf = take(qr64 ? 0 : 4 * (size_t)Mrp * (M + 1));
     L.Bd = take(qr64 ? 8 * (size_t)Mrp * (M + 1) : 0);
     L.Ct = take(4 * 2 * kTileB * (size_t)Mp);
     L.Ats = take(4 * 2 * kTileB * (size_t)Mrp);
@@ -189,15 +191,16 @@ __device__ void hyperpair_residual(const DevModel &m, const float *phiB, const u
 }
 
 // Phase C: B[:, 0..M-1] = A C (C = J Phi_s), B[:, M] = A r; B column-major
-// (ld Mrp), FP32.  Each tile of 16 bodies (32 dofs) stages its rows of A^T
+// (ld Mrp), FP32 products, each tile's sums added to B in TB (FP32 or FP64).  Each tile of 16 bodies (32 dofs) stages its rows of A^T
 // and of C in shared memory with one cooperative round of loads; threads own
 // 4x4 blocks of B (several each for large M, M_r) and add each tile's
 // contribution to them in shared memory.
+template <typename TB>
 __device__ void assemble_lsq(const DevModel &m, const float *phiB, const float *At, const float *D, const float *r,
-                             float *Ct, float *Ats, float *B) {
+                             float *Ct, float *Ats, TB *B) {
     const float h = (float)(0.5 * m.dt);
     const int tilesM = m.Mp / 4, tilesR = m.Mrp / 4, nblk = tilesM * tilesR;
-    for (int e = threadIdx.x; e < m.Mrp * (m.M + 1); e += kPT) B[e] = 0.f;
+    for (int e = threadIdx.x; e < m.Mrp * (m.M + 1); e += kPT) B[e] = TB(0);
     for (int i0 = 0; i0 < m.ns; i0 += kTileB) {
         const int nbt = min(kTileB, m.ns - i0);
         // stage the tile's A^T rows (slot 2j = chi dof of body i0+j, 2j+1 = psi dof)
@@ -250,8 +253,8 @@ __device__ void assemble_lsq(const DevModel &m, const float *phiB, const float *
                 if (r0 + x >= m.Mr) continue;
 #pragma unroll
                 for (int y = 0; y < 4; ++y)
-                    if (m0 + y < m.M) B[(size_t)(m0 + y) * m.Mrp + r0 + x] += acc[x][y];
-                if (m0 == 0) B[(size_t)m.M * m.Mrp + r0 + x] += bacc[x];
+                    if (m0 + y < m.M) B[(size_t)(m0 + y) * m.Mrp + r0 + x] += (TB)acc[x][y];
+                if (m0 == 0) B[(size_t)m.M * m.Mrp + r0 + x] += (TB)bacc[x];
             }
         }
         __syncthreads();
@@ -259,13 +262,14 @@ __device__ void assemble_lsq(const DevModel &m, const float *phiB, const float *
 }
 
 // eps numerator: || (A C)^T (A r) || from B = [A C | A r] (before the QR).
-__device__ float lsq_gradient(const DevModel &m, const float *B, float *red) {
+template <typename TB>
+__device__ float lsq_gradient(const DevModel &m, const TB *B, float *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float *b = B + (size_t)m.M * m.Mrp;
+    const TB *b = B + (size_t)m.M * m.Mrp;
     float g2 = 0.f;
     for (int k = warp; k < m.M; k += kPT / 32) {
         float s = 0.f;
-        for (int i = lane; i < m.Mr; i += 32) s = fmaf(B[(size_t)k * m.Mrp + i], b[i], s);
+        for (int i = lane; i < m.Mr; i += 32) s = fmaf((float)B[(size_t)k * m.Mrp + i], (float)b[i], s);
         s = warp_allsum(s);
         if (lane == 0) g2 += s * s;
     }
@@ -420,13 +424,14 @@ k_ptrom(const InstArgs *__restrict__ insts, int nsteps, DevStats *stats) {
         while (true) {
             gather_clusters(m, xh, xp, xhf, df, xq);
             hyperpair_residual(m, phiB, idx16, xhf, df, xq, gq, fp, f, D, r);
-            assemble_lsq(m, phiB, At, D, r, Ct, Ats, Bf);
-            const float g = lsq_gradient(m, Bf, red);
+            float g;
             if (m.qr64) {
-                for (int e = threadIdx.x; e < m.Mrp * (m.M + 1); e += kPT) Bd[e] = (double)Bf[e];
-                __syncthreads();
+                assemble_lsq(m, phiB, At, D, r, Ct, Ats, Bd);
+                g = lsq_gradient(m, Bd, red);
                 lsq_solve<double>(m, Bd, dx);
             } else {
+                assemble_lsq(m, phiB, At, D, r, Ct, Ats, Bf);
+                g = lsq_gradient(m, Bf, red);
                 lsq_solve<float>(m, Bf, dx);
             }
             for (int k = threadIdx.x; k < m.M; k += kPT) xh[k] += dx[k];

@@ -1119,20 +1119,37 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_TRY(pod_device(nd, nres, R, Mr_eff, st, Phir, sigr, true));
     std::vector<int> sampled = greedy_sample(Phir, n, Mr_eff, ns);
     if ((int)sampled.size() != ns) return set_error(PTROM_EINVAL, "ptrom_build: sampling found %zu bodies", sampled.size());
-    // A = [P Phi_r]^+ : (2ns x Mr) full column rank -> least squares with B = I
+    // A = [P Phi_r]^+ (Moore-Penrose, Eq. gappySolution).  P Phi_r is
+    // n_d x M_r.  With n_d >= M_r and full column rank, A solves
+    // min ||P Phi_r X - I||; with n_d < M_r (the gappy problem is then
+    // under-determined: the paper's mushroom cloud has n_d = 150 < M_r = 185)
+    // A is the minimum-norm right inverse, the transpose of (Phi_r^T P^T)^+.
     const int m2 = 2 * ns;
-    std::vector<double> PP((size_t)m2 * Mr_eff), Iden((size_t)m2 * m2, 0.0), X;
-    for (int s = 0; s < ns; ++s)
-        for (int c = 0; c < Mr_eff; ++c) {
-            PP[(size_t)c * m2 + s] = Phir[(size_t)sampled[s] * Mr_eff + c];
-            PP[(size_t)c * m2 + ns + s] = Phir[(size_t)(n + sampled[s]) * Mr_eff + c];
-        }
-    for (int d = 0; d < m2; ++d) Iden[(size_t)d * m2 + d] = 1.0;
-    if (!lstsq_qr(m2, Mr_eff, PP, Iden, m2, X))
-        return set_error(PTROM_EINVAL, "ptrom_build: P Phi_r is rank deficient (n_s too small for M_r)");
-    std::vector<double> Ah((size_t)Mr_eff * m2);  // X is Mr x m2 col-major per column of I
-    for (int d = 0; d < m2; ++d)
-        for (int r = 0; r < Mr_eff; ++r) Ah[(size_t)r * m2 + d] = X[(size_t)d * Mr_eff + r];
+    std::vector<double> Ah((size_t)Mr_eff * m2), X;
+    if (m2 >= Mr_eff) {
+        std::vector<double> PP((size_t)m2 * Mr_eff), Iden((size_t)m2 * m2, 0.0);
+        for (int s = 0; s < ns; ++s)
+            for (int c = 0; c < Mr_eff; ++c) {
+                PP[(size_t)c * m2 + s] = Phir[(size_t)sampled[s] * Mr_eff + c];
+                PP[(size_t)c * m2 + ns + s] = Phir[(size_t)(n + sampled[s]) * Mr_eff + c];
+            }
+        for (int d = 0; d < m2; ++d) Iden[(size_t)d * m2 + d] = 1.0;
+        if (!lstsq_qr(m2, Mr_eff, PP, Iden, m2, X))
+            return set_error(PTROM_EINVAL, "ptrom_build: P Phi_r is rank deficient");
+        for (int d = 0; d < m2; ++d)  // X is Mr x m2, column-major per column of I
+            for (int r = 0; r < Mr_eff; ++r) Ah[(size_t)r * m2 + d] = X[(size_t)d * Mr_eff + r];
+    } else {
+        std::vector<double> PT((size_t)Mr_eff * m2), Iden((size_t)Mr_eff * Mr_eff, 0.0);
+        for (int s = 0; s < ns; ++s)  // column d of (P Phi_r)^T = row d of P Phi_r
+            for (int c = 0; c < Mr_eff; ++c) {
+                PT[(size_t)s * Mr_eff + c] = Phir[(size_t)sampled[s] * Mr_eff + c];
+                PT[(size_t)(ns + s) * Mr_eff + c] = Phir[(size_t)(n + sampled[s]) * Mr_eff + c];
+            }
+        for (int r = 0; r < Mr_eff; ++r) Iden[(size_t)r * Mr_eff + r] = 1.0;
+        if (!lstsq_qr(Mr_eff, m2, PT, Iden, Mr_eff, X))
+            return set_error(PTROM_EINVAL, "ptrom_build: P Phi_r does not have full row rank");
+        Ah = X;  // column r of X is row r of A
+    }
     // clusters of the sampled bodies, numbered by first appearance
     std::vector<int> off(ns + 1, 0), idx;
     std::vector<int> remap(NcA, -1), order;

@@ -223,8 +223,10 @@ def test_mushroom_fom_fp32c_against_oracle(P):
     params = P.fom_params(M["dt"], M["delta"], "jfnk", prec="fp32c")
     traj, _ = _gpu_rollout_inflow(P, x0, G, u, params, 40, "fp32c")
     ref, _ = fom.rollout(x0, G, M["delta"], M["dt"], 40, mode="dense", tol=1e-13, u_inf=u)
-    disp = np.abs(ref - x0).max()
-    assert np.abs(traj - ref).max() <= 1e-5 * disp
+    # each FP32C step stops at ||r|| <= 1e-8 ||x|| (positions up to 75 from
+    # the origin body), so the gap may grow by that much per step
+    bound = 40 * 1e-8 * np.linalg.norm(ref, axis=1).max()
+    assert np.abs(traj - ref).max() <= bound, (np.abs(traj - ref).max(), bound)
     params64 = P.fom_params(M["dt"], M["delta"], "blockdiag", tol=1e-13, prec="fp64")
     still, _ = _gpu_rollout_inflow(P, x0, np.zeros(500), u, params64, 3, "fp64")
     np.testing.assert_allclose(still, x0 + np.arange(4)[:, None] * M["dt"] * u, rtol=0, atol=1e-12)

@@ -271,3 +271,18 @@ def test_inflow_model_save_load_and_clear(P, tmp_path):
     assert np.abs(c - a).max() > 1e-3 * np.abs(a).max()
     model.set_inflow_full(_dev(u))
     np.testing.assert_array_equal(run(model), a)
+
+
+def test_more_residual_modes_than_sampled_dofs(P):
+    """M_r > n_d: A = [P Phi_r]^+ is the minimum-norm right inverse (M_r x n_d,
+    full column rank), and the online model built with it runs."""
+    x0, G = W.two_cluster(512, seed=0)
+    fp = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c")
+    model, info = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 10, 32, 12, 60, fp, theta=0.5)
+    A = model.query()["A"]
+    assert A.shape == (32, 24)
+    assert np.linalg.matrix_rank(A) == 24
+    st = model.new_state()
+    hist = torch.zeros(60, 10, dtype=torch.float64, device="cuda")
+    s = P.ptrom_step([model], [st], 60, hist=[hist])
+    assert np.isfinite(hist.cpu().numpy()).all() and s["steps"] == 60

@@ -132,6 +132,30 @@ def test_greedy_sampling_small_case():
     np.testing.assert_allclose(A @ Phi_r[dofs], np.eye(Mr), atol=1e-12)
 
 
+def test_gappy_operator_with_more_residual_modes_than_sampled_dofs():
+    """M_r > n_d (the mushroom cloud of Sec. 6.3: M_r = 185, n_d = 150): the
+    least squares of Eq. approx_resi is under-determined and [P Phi_r]^+ is
+    the minimum-norm solution operator.  It is a right inverse of P Phi_r,
+    its rows lie in the row space of P Phi_r, and sampling is still n_s
+    distinct bodies chosen from the first n_c = n_d modes."""
+    rng = np.random.default_rng(8)
+    N, Mr, ns = 40, 14, 5
+    Phi_r, _ = np.linalg.qr(rng.standard_normal((2 * N, Mr)))
+    s = rom.greedy_sample(Phi_r, ns, N)
+    assert len(set(s)) == ns
+    dofs = np.concatenate([s, N + s])
+    PPr = Phi_r[dofs]                              # n_d x M_r = 10 x 14
+    A = rom.gappy_operator(Phi_r, s, N)
+    assert A.shape == (Mr, 2 * ns)
+    np.testing.assert_allclose(PPr @ A, np.eye(2 * ns), atol=1e-12)
+    # minimum norm: A's columns are combinations of P Phi_r's rows
+    coef = np.linalg.lstsq(PPr.T, A, rcond=None)[0]
+    np.testing.assert_allclose(PPr.T @ coef, A, atol=1e-12)
+    # any other right inverse has a larger Frobenius norm
+    Z = (np.eye(Mr) - np.linalg.pinv(PPr) @ PPr) @ rng.standard_normal((Mr, 2 * ns))
+    assert np.linalg.norm(A + Z) > np.linalg.norm(A)
+
+
 def test_ptrom_reproduces_fom_when_basis_spans_trajectory():
     """A basis spanning the state space (as many independent snapshots as
     dofs), every body sampled, no clustering: the PTROM trajectory is the FOM
