@@ -124,6 +124,21 @@ def _dist():
     return rank, local, ws
 
 
+def aggregate_ranks(ms, units, device, ws):
+    """Whole-job figures of a replicas run: the slowest rank's timed
+    milliseconds and the units every rank processed.  Collective over the
+    default process group when ws > 1 (NCCL on GPUs, gloo in the CPU tests)."""
+    if ws <= 1:
+        return float(ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 # --------------------------------------------------------------------- oracle
 def run_reference(args):
     """The FP64 CPU oracle on the host cores: per step, the pair sums one FOM
@@ -258,15 +273,7 @@ def run_ours(args):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     pairs = (agg["velocity_evals"] + agg["jvp_evals"]) * n * n
 
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(pairs)], device=dev, dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_all, pairs_all = float(tmax[0]), float(t[1])
-    else:
-        ms_all, pairs_all = ms, float(pairs)
+    ms_all, pairs_all = aggregate_ranks(ms, pairs, dev, ws)
     value = pairs_all / (ms_all * 1e-3)
 
     # roofline of the dominant kernel (largest event-timed total)

@@ -950,7 +950,8 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     const int NcA = (int)all.keys.size();
     inf.N_c_all = NcA;
     inf.mean_list_all = (double)all.idx.size() / n;
-    // cluster values for the first training parameter
+    // cluster values for the first training parameter (Tier II recomputes them for the
+    // others; the online model starts at this one)
     const int Mp = (M + 3) & ~3;
     std::vector<double> phicA((size_t)2 * NcA * M), x0cA(2 * (size_t)NcA), gcA(NcA);
     std::vector<int> mem;
