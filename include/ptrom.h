@@ -368,7 +368,8 @@ int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
  * ptrom_build -- the offline training of Sec. 5.1 for one or more training
  * parameters mu_p (circulations Gamma_p, initial states x0_p):
  *   Stage 1  FOM snapshots: the states x^n(mu_p), n = 1..steps (fom_step
- *            with the given FOM parameters), as Sec. 3.1 defines them;
+ *            with the given FOM parameters), as Sec. 3.1 defines them, or
+ *            the caller's (p->snapshots);
  *   Stage 2  POD Phi (M modes, Sec. 3.1) of all snapshots (exact: the
  *            eigenvectors of the smaller of S^T S and S S^T; randomized range
  *            finder with power iterations when min(2n, snapshots) exceeds
@@ -405,6 +406,9 @@ typedef struct ptrom_build_params {
     int qr_prec;           /* online least-squares precision                 */
     ptrom_fom_params fom;  /* Stage 1 FOM (dt and delta are the model's)     */
     const double *u_infs;  /* DEVICE [n_params][2n] inflow per parameter, or NULL */
+    const double *snapshots; /* DEVICE [n_params * steps][2n]: the caller's Stage 1
+                              states x^1..x^steps of each parameter in turn (read
+                              only), or NULL to run the FOM                    */
 } ptrom_build_params;
 
 typedef struct ptrom_build_info {

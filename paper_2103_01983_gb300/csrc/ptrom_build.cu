@@ -856,18 +856,19 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     ptrom_build_info inf{};
     const int nd = 2 * n, M = p->M, Mr = p->M_r, ns = p->n_s;
     const double dt = p->fom.dt, delta = p->fom.delta;
-    // ---------------- Stage 1: FOM snapshots
+    // ---------------- Stage 1: FOM snapshots (or the caller's)
     auto t0 = Clock::now();
     const int K = n_params * p->steps;
-    double *S = nullptr, *x = nullptr, *f = nullptr;
+    double *S_own = nullptr, *x = nullptr, *f = nullptr;
     void *work = nullptr;
     const size_t wbytes = fom_workspace_bytes(&p->fom, n);
     if (!wbytes) return set_error(PTROM_EINVAL, "ptrom_build: bad FOM parameters");
-    PTROM_TRY(scratch_alloc((void **)&S, sizeof(double) * (size_t)nd * K, st));
+    if (!p->snapshots) PTROM_TRY(scratch_alloc((void **)&S_own, sizeof(double) * (size_t)nd * K, st));
+    const double *S = p->snapshots ? p->snapshots : S_own;
     PTROM_TRY(scratch_alloc((void **)&x, sizeof(double) * nd, st));
     PTROM_TRY(scratch_alloc((void **)&f, sizeof(double) * nd, st));
     PTROM_TRY(scratch_alloc(&work, wbytes, st));
-    for (int q = 0; q < n_params; ++q) {
+    for (int q = 0; q < n_params && !p->snapshots; ++q) {
         const double *x0 = x0s + (size_t)q * nd, *G = gammas + (size_t)q * n;
         ptrom_fom_params fq = p->fom;
         fq.u_inf = p->u_infs ? p->u_infs + (size_t)q * nd : nullptr;
@@ -876,7 +877,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
         for (int s = 0; s < p->steps; ++s) {
             const int stt = fom_step(&fq, n, G, x, f, work, wbytes, nullptr, stream);
             if (stt != PTROM_OK && stt != PTROM_ENOCONV) return stt;
-            k_snapshot<<<(nd + 255) / 256, 256, 0, st>>>(nd, x, S + (size_t)(q * p->steps + s) * nd);
+            k_snapshot<<<(nd + 255) / 256, 256, 0, st>>>(nd, x, S_own + (size_t)(q * p->steps + s) * nd);
             count_launch();
         }
     }
@@ -1194,9 +1195,9 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     inf.mean_list = (double)idx.size() / ns;
     inf.seconds_sample = secs(t0);
     // free the stage buffers
-    for (void *b : std::vector<void *>{S, x, f, work, dphi, dx0, dphic, dx0c, dgc, dxt, dpd, dxq, dxh, ddx, df, dfp, dD,
-                                        dr, dpart, du, doff, didx, dout, R})
-        PTROM_TRY(scratch_free(b, st));
+    for (void *b : std::vector<void *>{S_own, x, f, work, dphi, dx0, dphic, dx0c, dgc, dxt, dpd, dxq, dxh, ddx, df, dfp,
+                                        dD, dr, dpart, du, doff, didx, dout, R})
+        if (b) PTROM_TRY(scratch_free(b, st));
     PTROM_CUDA(cudaStreamSynchronize(st));
     PTROM_TRY(scratch_trim());  // hand the training buffers back to the device
     // ---------------- the online model

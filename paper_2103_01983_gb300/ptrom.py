@@ -91,7 +91,7 @@ class BuildParams(ctypes.Structure):
     """Mirror of ptrom_build_params."""
     _fields_ = [("M", _i), ("M_r", _i), ("n_s", _i), ("criterion", _i), ("theta", _d), ("p_c", _d),
                 ("steps", _i), ("tol", _d), ("max_gn", _i), ("qr_prec", _i), ("fom", FomParams),
-                ("u_infs", _vp)]
+                ("u_infs", _vp), ("snapshots", _vp)]
 
 
 class BuildInfo(ctypes.Structure):
@@ -447,9 +447,10 @@ CRITERIA = {"bh": 0, "barnes_hut": 0, "nb": 1, "neighbor": 1}
 
 
 def ptrom_build(x0s, gammas, M, M_r, n_s, steps, fom, criterion="bh", theta=0.5, p_c=1.0, tol=1e-4,
-                max_gn=100, qr_prec="fp64", stream=None, u_infs=None):
+                max_gn=100, qr_prec="fp64", stream=None, u_infs=None, snapshots=None):
     """Offline training (Stages 1-4) from device tensors x0s [P, 2n], gammas [P, n]
-    and optionally u_infs [P, 2n] (superimposed inflow per parameter).
+    and optionally u_infs [P, 2n] (superimposed inflow per parameter) and
+    snapshots [P * steps, 2n] (the Stage 1 states, instead of running the FOM).
     Returns (PtromModel, info dict)."""
     x0s = x0s.contiguous()
     gammas = gammas.contiguous()
@@ -458,9 +459,13 @@ def ptrom_build(x0s, gammas, M, M_r, n_s, steps, fom, criterion="bh", theta=0.5,
         u_infs = u_infs.contiguous()
         if u_infs.shape != x0s.shape or u_infs.device != x0s.device:
             raise ValueError("u_infs must be shaped like x0s, on its device")
+    if snapshots is not None:
+        snapshots = snapshots.contiguous()
+        if tuple(snapshots.shape) != (P * int(steps), 2 * n) or snapshots.device != x0s.device:
+            raise ValueError("snapshots must be [P * steps, 2n] on the device of x0s")
     bp = BuildParams(int(M), int(M_r), int(n_s), CRITERIA[criterion], float(theta), float(p_c), int(steps),
                      float(tol), int(max_gn), _prec(qr_prec), fom,
-                     _ptr(u_infs))
+                     _ptr(u_infs), _ptr(snapshots))
     h = ctypes.c_void_p()
     info = BuildInfo()
     _check(lib.ptrom_build(ctypes.byref(bp), int(n), int(P), _ptr(x0s), _ptr(gammas), ctypes.byref(h),

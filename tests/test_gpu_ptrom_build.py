@@ -286,3 +286,28 @@ def test_more_residual_modes_than_sampled_dofs(P):
     hist = torch.zeros(60, 10, dtype=torch.float64, device="cuda")
     s = P.ptrom_step([model], [st], 60, hist=[hist])
     assert np.isfinite(hist.cpu().numpy()).all() and s["steps"] == 60
+
+
+def test_caller_snapshots_give_the_same_model(P):
+    """Stage 1 from the caller: the FOM trajectory handed in as snapshots
+    gives the model the library builds from its own FOM run, and the array
+    is left untouched."""
+    x0, G = W.two_cluster(512, seed=1)
+    steps = 40
+    fp = P.fom_params(0.005, 0.02, "jfnk", prec="fp64", tol=1e-12)
+    ref, _ = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 10, 20, 20, steps, fp, theta=0.5)
+    x, Gt = _dev(x0), _dev(G)
+    f = P.bs_velocity(x, Gt, 0.02, prec="fp64")
+    work = P.fom_workspace(fp, 512)
+    S = torch.empty(steps, 1024, dtype=torch.float64, device="cuda")
+    for k in range(steps):
+        P.fom_step(fp, Gt, x, f, work=work)
+        S[k] = x
+    S0 = S.clone()
+    got, info = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 10, 20, 20, steps, fp, theta=0.5, snapshots=S)
+    assert torch.equal(S, S0)
+    a, b = ref.query(), got.query()
+    np.testing.assert_array_equal(a["phi"], b["phi"])
+    np.testing.assert_array_equal(a["sampled"], b["sampled"])
+    np.testing.assert_array_equal(a["A"], b["A"])
+    assert info["n_snapshots"] == steps
