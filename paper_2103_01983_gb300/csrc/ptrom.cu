@@ -277,10 +277,15 @@ __device__ float lsq_gradient(const DevModel &m, const TB *B, float *red) {
 }
 
 // Householder QR of B (Mr x M, column-major, rhs in column M) in T arithmetic,
-// then dx = -R^{-1} (Q^T b)[0..M-1].  Every warp computes column j's
-// Householder vector itself from the same data (identical in all warps), so
-// one CTA barrier per column suffices: warps then update the later columns
-// k = j+1+warp, j+1+warp+16, ... in parallel.
+// then dx = -R^{-1} (Q^T b)[0..M-1].  One CTA barrier per column: warps
+// update the later columns in parallel (in FP64 four per warp: warp w takes
+// j+1+4w .. j+4+4w, then the next 64; in FP32 one: j+1+w, then the next 16),
+// and the warp that owns column j+1 (warp 0) derives that column's reflector
+// as soon as its own update of it is done, before the barrier.  The reflector's
+// square root and division thus run once per column, not in every warp: in
+// FP64 a warp-wide instruction holds a sub-partition's FP64 unit for ~64
+// cycles whatever its active lanes, so sixteen redundant copies would cost
+// more than the rest of the column.
 template <typename T>
 __device__ __forceinline__ T warp_allsum_t(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -295,11 +300,40 @@ __device__ __forceinline__ double ls_rcp(double v) { return 1.0 / v; }
 __device__ __forceinline__ float ls_sqrt(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
 __device__ __forceinline__ float ls_rcp(float v) { return rcp_approx(v); }
 
+// Reflector of column j (called by one whole warp; the values are warp-
+// uniform): v = (x0 - alpha, c_j[j+1..]), H = I - tau v v^T, with
+// alpha = -sign(x0) |c_j[j..]|.  The squared norm comes from the downdated
+// s_rem unless half of it is gone (each downdate errs by ~eps |c_j|^2 <=
+// eps s_ref, so the value is good to ~40 eps while half remains), in which
+// case it is summed again.  Writes alpha, v0 and tau to slot j & 1.
+template <typename T>
+__device__ __forceinline__ void reflector(const T *cj, int j, int Mr, int lane, const T *s_rem, const T *s_ref,
+                                          T *s_alpha, T (*s_scal)[2]) {
+    T s = s_rem[j];
+    if (!(s >= (T)0.5 * s_ref[j])) {
+        s = 0;
+        for (int i = j + lane; i < Mr; i += 32) s += cj[i] * cj[i];
+        s = warp_allsum_t(s);
+    }
+    const T x0 = cj[j];
+    const T nrm = ls_sqrt(s);
+    const T alpha = x0 >= 0 ? -nrm : nrm;
+    const T v0 = x0 - alpha;
+    const T vn2 = s - x0 * x0 + v0 * v0;
+    const T tau = vn2 > 0 ? (T)2 * ls_rcp(vn2) : (T)0;
+    if (lane == 0) {
+        s_alpha[j] = alpha;
+        s_scal[j & 1][0] = v0;
+        s_scal[j & 1][1] = tau;
+    }
+}
+
 template <typename T>
 __device__ void lsq_solve(const DevModel &m, T *B, double *dx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Mr = m.Mr, M = m.M, ld = m.Mrp;
     __shared__ T s_alpha[kMaxM], s_y[kMaxM], s_rem[kMaxM], s_ref[kMaxM];
+    __shared__ T s_scal[2][2];  // (v0, tau) of column j in slot j & 1
     const int ncols = min(M, Mr);
     // remaining squared norm of every column over the rows not yet reduced
     // (downdated after each reflection: |c_k[j..]|^2 = |c_k[j-1..]|^2 - R_{j-1,k}^2,
@@ -312,41 +346,49 @@ __device__ void lsq_solve(const DevModel &m, T *B, double *dx) {
         if (lane == 0) s_rem[k] = s_ref[k] = s;
     }
     __syncthreads();
+    if (warp == 0 && ncols > 0) reflector(B, 0, Mr, lane, s_rem, s_ref, s_alpha, s_scal);
+    __syncthreads();
+    // FP64: each warp updates kCols = 4 columns at once, kG = 8 lanes per
+    // column, so a warp instruction carries four columns' work on the scarce
+    // FP64 unit (and the dot products need three shuffle levels instead of
+    // five).  FP32 is latency-bound instead: one column per warp, 32 lanes.
+    constexpr int kG = sizeof(T) == 8 ? 8 : 32, kCols = 32 / kG;
+    const int sub = lane / kG, gl = lane % kG;
     for (int j = 0; j < ncols; ++j) {
         const T *cj = B + (size_t)j * ld;
-        T s = s_rem[j];
-        // each downdate errs by ~eps |c_j|^2 <= eps s_ref: while half of the
-        // norm remains the value is good to ~40 eps; otherwise sum it again
-        // (the same branch in every warp: the values are shared)
-        if (!(s >= (T)0.5 * s_ref[j])) {
-            s = 0;
-            for (int i = j + lane; i < Mr; i += 32) s += cj[i] * cj[i];
-            s = warp_allsum_t(s);
-        }
-        const T x0 = cj[j];
-        const T nrm = ls_sqrt(s);
-        const T alpha = x0 >= 0 ? -nrm : nrm;
-        const T v0 = x0 - alpha;  // v = (v0, cj[j+1..])
-        const T vn2 = s - x0 * x0 + v0 * v0;
-        const T tau = vn2 > 0 ? (T)2 * ls_rcp(vn2) : (T)0;
-        if (threadIdx.x == 0) s_alpha[j] = alpha;
-        for (int k = j + 1 + warp; k <= M; k += kPT / 32) {
+        const T v0 = s_scal[j & 1][0], tau = s_scal[j & 1][1];
+        for (int kb = j + 1 + warp * kCols; kb <= M; kb += (kPT / 32) * kCols) {
+            const int k = kb + sub;
+            const bool act = k <= M;  // uniform within each group of kG lanes
             T *ck = B + (size_t)k * ld;
             T w = 0;
-            for (int i = j + lane; i < Mr; i += 32) w += (i == j ? v0 : cj[i]) * ck[i];
-            w = warp_allsum_t(w) * tau;
-            for (int i = j + lane; i < Mr; i += 32) {
-                const T c = ck[i] - w * (i == j ? v0 : cj[i]);
-                ck[i] = c;
-                if (i == j && k < ncols) s_rem[k] -= c * c;  // row j of column k is now R_jk
+            if (act)
+                for (int i = j + gl; i < Mr; i += kG) w += (i == j ? v0 : cj[i]) * ck[i];
+            for (int o = kG / 2; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            w *= tau;
+            if (act)
+                for (int i = j + gl; i < Mr; i += kG) {
+                    const T c = ck[i] - w * (i == j ? v0 : cj[i]);
+                    ck[i] = c;
+                    if (i == j && k < ncols) s_rem[k] -= c * c;  // row j of column k is now R_jk
+                }
+            if (kb == j + 1 && kb < ncols) {  // warp 0: column j+1 is final for step j+1
+                __syncwarp();
+                reflector(B + (size_t)kb * ld, kb, Mr, lane, s_rem, s_ref, s_alpha, s_scal);
             }
         }
-        __syncthreads();  // the updated columns (and remaining norms) are read by every warp next
+        __syncthreads();  // the updated columns and the next reflector are read by every warp next
     }
+    // 1 / R_jj for every column at once (s_rem is free now), off the
+    // back substitution's dependent chain
+    for (int j = threadIdx.x; j < ncols; j += kPT) s_rem[j] = s_alpha[j] != 0 ? ls_rcp(s_alpha[j]) : (T)0;
+    __syncthreads();
     // back substitution R y = -c (warp 0, in T), column by column: lane l
-    // holds the right-hand sides of rows l and l + 32; each step broadcasts
+    // holds the right-hand sides of rows l, l + 32, ...; each step broadcasts
     // y_j from its row's lane and updates the rows above it (R_ij is column
-    // j's row i; R's diagonal is s_alpha), one shuffle and one FMA per step
+    // j's row i), one shuffle and one multiply-add per step; the row blocks
+    // entirely below j are skipped (warp-uniform), since even lanes switched
+    // off by a predicate occupy the FP64 unit
     if (warp == 0) {
         const T *rhs = B + (size_t)M * ld;
         constexpr int kQ = kMaxM / 32;  // rows per lane
@@ -358,13 +400,12 @@ __device__ void lsq_solve(const DevModel &m, T *B, double *dx) {
 #pragma unroll
             for (int q = 1; q < kQ; ++q) own = (j >> 5) == q ? c[q] : own;
             const T cj = __shfl_sync(0xffffffffu, own, j & 31);
-            const T rjj = s_alpha[j];
-            const T yj = rjj != 0 ? cj * ls_rcp(rjj) : (T)0;
+            const T yj = cj * s_rem[j];
             if (lane == (j & 31)) s_y[j] = yj;
             const T *cjc = B + (size_t)j * ld;
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                if (lane + 32 * q < j) c[q] -= cjc[lane + 32 * q] * yj;
+                if (32 * q < j && lane + 32 * q < j) c[q] -= cjc[lane + 32 * q] * yj;
         }
     }
     __syncthreads();
