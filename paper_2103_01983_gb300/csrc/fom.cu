@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "scratch.h"
 #include "internal.h"
 
 namespace ptrom {
@@ -1492,8 +1493,9 @@ extern "C" int fom_step_batched(const ptrom_fom_params *p, int B, const int *n, 
     const int rg = std::min(red_grid(2 * maxn), 2 * device_sm_count());
     BInst *dinst = nullptr;
     double *dnorm = nullptr;
-    PTROM_TRY(scratch_alloc((void **)&dinst, sizeof(BInst) * B, st));
-    PTROM_TRY(scratch_alloc((void **)&dnorm, sizeof(double) * 2 * B, st));
+    ScratchScope sc(st);
+    PTROM_TRY(sc.alloc(&dinst, sizeof(BInst) * B));
+    PTROM_TRY(sc.alloc(&dnorm, sizeof(double) * 2 * B));
     std::vector<int> active(B);
     for (int b = 0; b < B; ++b) active[b] = b;
     std::vector<double> norms(2 * B);
@@ -1557,8 +1559,7 @@ extern "C" int fom_step_batched(const ptrom_fom_params *p, int B, const int *n, 
         }
         active.swap(next);
     }
-    PTROM_TRY(scratch_free(dinst, st));
-    PTROM_TRY(scratch_free(dnorm, st));
+    PTROM_TRY(sc.release());
     PTROM_CUDA(cudaStreamSynchronize(st));
     return status;
 }

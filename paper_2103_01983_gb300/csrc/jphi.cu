@@ -11,6 +11,7 @@
 // through atomic adds (the output is zeroed first).  An FP64 variant (one
 // thread per target and column) serves checking.
 #include "common.cuh"
+#include "scratch.h"
 #include "internal.h"
 
 namespace ptrom {
@@ -178,7 +179,8 @@ int jphi(int n, const double *x, const double *G, double delta, const double *ph
         while ((long long)tblocks * nslices * S * 2 <= want && (S * 2) * 4 <= nchunks) S *= 2;
     }
     JRec *packed = nullptr;
-    PTROM_TRY(scratch_alloc((void **)&packed, sizeof(JRec) * (size_t)nslices * ns_pad, st));
+    ScratchScope sc(st);
+    PTROM_TRY(sc.alloc(&packed, sizeof(JRec) * (size_t)nslices * ns_pad));
     int pgrid = (nslices * ns_pad + 255) / 256;
     if (pgrid > 8 * device_sm_count()) pgrid = 8 * device_sm_count();
     k_jphi_pack<<<pgrid, 256, 0, st>>>(n, x, G, phi, M, nslices, ns_pad, packed);
@@ -192,7 +194,7 @@ int jphi(int n, const double *x, const double *G, double delta, const double *ph
         k_jphi<false><<<grid, kJT, 0, st>>>(n, x, phi, M, (float)delta, packed, ns_pad, nchunks, out);
     timing_end(slot, st);
     const cudaError_t e = cudaGetLastError();
-    PTROM_TRY(scratch_free(packed, st));
+    PTROM_TRY(sc.release());
     if (e != cudaSuccess) return check_cuda(e, "k_jphi launch");
     count_launch();
     return PTROM_OK;

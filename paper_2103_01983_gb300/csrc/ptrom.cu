@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "scratch.h"
 #include "internal.h"
 #include "ptrom_model.h"
 
@@ -715,7 +716,8 @@ extern "C" int ptrom_step(ptrom_model *const *models, int batch, void *const *st
     }
     void *dev = nullptr;
     const size_t bytes = sizeof(InstArgs) * batch + sizeof(DevStats);
-    PTROM_TRY(scratch_alloc(&dev, bytes, st));
+    ScratchScope sc(st);
+    PTROM_TRY(sc.alloc(&dev, bytes));
     InstArgs *dinst = (InstArgs *)dev;
     DevStats *dstats = (DevStats *)((char *)dev + sizeof(InstArgs) * batch);
     PTROM_CUDA(cudaMemcpyAsync(dinst, host.data(), sizeof(InstArgs) * batch, cudaMemcpyHostToDevice, st));
@@ -725,10 +727,7 @@ extern "C" int ptrom_step(ptrom_model *const *models, int batch, void *const *st
     k_ptrom<<<batch, kPT, smem, st>>>(dinst, nsteps, dstats);
     timing_end(slot, st);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        scratch_free(dev, st);
-        return check_cuda(e, "k_ptrom launch");
-    }
+    if (e != cudaSuccess) return check_cuda(e, "k_ptrom launch");
     count_launch();
     if (stats) {
         DevStats hs{};
@@ -739,6 +738,5 @@ extern "C" int ptrom_step(ptrom_model *const *models, int batch, void *const *st
         stats->noconv = hs.noconv;
         stats->max_iters = hs.max_iters;
     }
-    PTROM_TRY(scratch_free(dev, st));
-    return PTROM_OK;
+    return sc.release();
 }

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "ptrom_model.h"
+#include "scratch.h"
 #include "symeig.h"
 
 namespace ptrom {
@@ -30,6 +31,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 double secs(Clock::time_point a) { return std::chrono::duration<double>(Clock::now() - a).count(); }
+
 
 // ------------------------------------------------------------------ host dense algebra
 // Eigen-decomposition of a symmetric n x n matrix (row-major) by cyclic
@@ -608,13 +610,14 @@ static int pod_randomized(int nd, int K, const double *S, int &M, cudaStream_t s
     int r = std::min(M + 32, std::min(nd, K));
     const int r0 = r;
     double *Om, *Y, *Z, *T, *Gd, *Wd, *Bm;
-    PTROM_TRY(scratch_alloc((void **)&Om, sizeof(double) * (size_t)K * r0, st));
-    PTROM_TRY(scratch_alloc((void **)&Y, sizeof(double) * (size_t)nd * r0, st));
-    PTROM_TRY(scratch_alloc((void **)&Z, sizeof(double) * (size_t)K * r0, st));
-    PTROM_TRY(scratch_alloc((void **)&T, sizeof(double) * (size_t)std::max(nd, K) * r0, st));
-    PTROM_TRY(scratch_alloc((void **)&Gd, sizeof(double) * (size_t)r0 * r0, st));
-    PTROM_TRY(scratch_alloc((void **)&Wd, sizeof(double) * (size_t)r0 * r0, st));
-    PTROM_TRY(scratch_alloc((void **)&Bm, sizeof(double) * (size_t)r0 * K, st));
+    ScratchScope sc(st);
+    PTROM_TRY(sc.alloc(&Om, sizeof(double) * (size_t)K * r0));
+    PTROM_TRY(sc.alloc(&Y, sizeof(double) * (size_t)nd * r0));
+    PTROM_TRY(sc.alloc(&Z, sizeof(double) * (size_t)K * r0));
+    PTROM_TRY(sc.alloc(&T, sizeof(double) * (size_t)std::max(nd, K) * r0));
+    PTROM_TRY(sc.alloc(&Gd, sizeof(double) * (size_t)r0 * r0));
+    PTROM_TRY(sc.alloc(&Wd, sizeof(double) * (size_t)r0 * r0));
+    PTROM_TRY(sc.alloc(&Bm, sizeof(double) * (size_t)r0 * K));
     {
         std::vector<double> om((size_t)K * r0);
         std::mt19937_64 rng(20210302ull);
@@ -657,7 +660,7 @@ static int pod_randomized(int nd, int K, const double *S, int &M, cudaStream_t s
     std::vector<double> P((size_t)nd * M);
     PTROM_CUDA(cudaMemcpyAsync(P.data(), T, sizeof(double) * P.size(), cudaMemcpyDeviceToHost, st));
     PTROM_CUDA(cudaStreamSynchronize(st));
-    for (double *b : {Om, Y, Z, T, Gd, Wd, Bm}) PTROM_TRY(scratch_free(b, st));
+    PTROM_TRY(sc.release());
     Phi.resize((size_t)nd * M);
     for (int m = 0; m < M; ++m) {
         int best = 0;
@@ -682,14 +685,15 @@ int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vec
     if (std::min(nd, K) > g_pod_exact_max.load()) return pod_randomized(nd, K, S, M, st, Phi, sigma, clamp);
     if (nd < K) {
         double *C = nullptr;
-        PTROM_TRY(scratch_alloc((void **)&C, sizeof(double) * (size_t)nd * nd, st));
+        ScratchScope sc(st);
+        PTROM_TRY(sc.alloc(&C, sizeof(double) * (size_t)nd * nd));
         dim3 grid((nd + 31) / 32, (nd + 31) / 32);
         k_cov<<<grid, 256, 0, st>>>(nd, K, S, C);
         count_launch();
         std::vector<double> Ch((size_t)nd * nd);
         PTROM_CUDA(cudaMemcpyAsync(Ch.data(), C, sizeof(double) * Ch.size(), cudaMemcpyDeviceToHost, st));
         PTROM_CUDA(cudaStreamSynchronize(st));
-        PTROM_TRY(scratch_free(C, st));
+        PTROM_TRY(sc.release());
         for (int a = 0; a < nd; ++a)
             for (int b = 0; b < a; ++b) Ch[(size_t)a * nd + b] = Ch[(size_t)b * nd + a];
         std::vector<double> w, V;
@@ -716,14 +720,15 @@ int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vec
         return PTROM_OK;
     }
     double *G = nullptr, *Wd = nullptr, *Pd = nullptr;
-    PTROM_TRY(scratch_alloc((void **)&G, sizeof(double) * (size_t)K * K, st));
+    ScratchScope sc(st);
+    PTROM_TRY(sc.alloc(&G, sizeof(double) * (size_t)K * K));
     dim3 grid((K + 31) / 32, (K + 31) / 32);
     k_gram<<<grid, 256, 0, st>>>(nd, K, S, G);
     count_launch();
     std::vector<double> Gh((size_t)K * K);
     PTROM_CUDA(cudaMemcpyAsync(Gh.data(), G, sizeof(double) * Gh.size(), cudaMemcpyDeviceToHost, st));
     PTROM_CUDA(cudaStreamSynchronize(st));
-    PTROM_TRY(scratch_free(G, st));
+    PTROM_TRY(sc.release());
     for (int a = 0; a < K; ++a)
         for (int b = 0; b < a; ++b) Gh[(size_t)a * K + b] = Gh[(size_t)b * K + a];
     std::vector<double> w, V;
@@ -740,16 +745,15 @@ int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vec
         sigma[m] = sqrt(w[m]);
         for (int k = 0; k < K; ++k) Wm[(size_t)k * M + m] = V[(size_t)k * K + m] / sigma[m];
     }
-    PTROM_TRY(scratch_alloc((void **)&Wd, sizeof(double) * Wm.size(), st));
-    PTROM_TRY(scratch_alloc((void **)&Pd, sizeof(double) * (size_t)nd * M, st));
+    PTROM_TRY(sc.alloc(&Wd, sizeof(double) * Wm.size()));
+    PTROM_TRY(sc.alloc(&Pd, sizeof(double) * (size_t)nd * M));
     PTROM_CUDA(cudaMemcpyAsync(Wd, Wm.data(), sizeof(double) * Wm.size(), cudaMemcpyHostToDevice, st));
     k_combine<<<(nd + 127) / 128, 128, 0, st>>>(nd, K, M, S, Wd, Pd);
     count_launch();
     Phi.resize((size_t)nd * M);
     PTROM_CUDA(cudaMemcpyAsync(Phi.data(), Pd, sizeof(double) * Phi.size(), cudaMemcpyDeviceToHost, st));
     PTROM_CUDA(cudaStreamSynchronize(st));
-    PTROM_TRY(scratch_free(Wd, st));
-    PTROM_TRY(scratch_free(Pd, st));
+    PTROM_TRY(sc.release());
     // Phi = S V / sigma loses orthogonality for modes with tiny sigma (the Gram
     // matrix squares the condition number); two modified Gram-Schmidt passes
     // restore orthonormal columns.
@@ -863,11 +867,12 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     void *work = nullptr;
     const size_t wbytes = fom_workspace_bytes(&p->fom, n);
     if (!wbytes) return set_error(PTROM_EINVAL, "ptrom_build: bad FOM parameters");
-    if (!p->snapshots) PTROM_TRY(scratch_alloc((void **)&S_own, sizeof(double) * (size_t)nd * K, st));
+    ScratchScope sc(st);  // every training buffer below, released on all paths
+    if (!p->snapshots) PTROM_TRY(sc.alloc(&S_own, sizeof(double) * (size_t)nd * K));
     const double *S = p->snapshots ? p->snapshots : S_own;
-    PTROM_TRY(scratch_alloc((void **)&x, sizeof(double) * nd, st));
-    PTROM_TRY(scratch_alloc((void **)&f, sizeof(double) * nd, st));
-    PTROM_TRY(scratch_alloc(&work, wbytes, st));
+    PTROM_TRY(sc.alloc(&x, sizeof(double) * nd));
+    PTROM_TRY(sc.alloc(&f, sizeof(double) * nd));
+    PTROM_TRY(sc.alloc(&work, wbytes));
     for (int q = 0; q < n_params && !p->snapshots; ++q) {
         const double *x0 = x0s + (size_t)q * nd, *G = gammas + (size_t)q * n;
         ptrom_fom_params fq = p->fom;
@@ -981,7 +986,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     float *dphi, *dx0, *dphic, *dx0c, *dgc, *dxt, *dpd, *dxq, *dxh, *ddx, *df, *dfp, *dD, *dr, *dpart, *du;
     int *doff, *didx;
     double *dout, *R;
-    auto falloc = [&](float **pp, size_t cnt) { return scratch_alloc((void **)pp, sizeof(float) * std::max<size_t>(cnt, 4), st); };
+    auto falloc = [&](float **pp, size_t cnt) { return sc.alloc(pp, sizeof(float) * std::max<size_t>(cnt, 4)); };
     PTROM_TRY(falloc(&dphi, phif.size()));
     PTROM_TRY(falloc(&dx0, nd));
     PTROM_TRY(falloc(&dphic, phicf.size()));
@@ -998,10 +1003,10 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_TRY(falloc(&dr, nd));
     PTROM_TRY(falloc(&dpart, (size_t)nblk * nout));
     PTROM_TRY(falloc(&du, nd));
-    PTROM_TRY(scratch_alloc((void **)&doff, sizeof(int) * (n + 1), st));
-    PTROM_TRY(scratch_alloc((void **)&didx, sizeof(int) * std::max<size_t>(all.idx.size(), 1), st));
-    PTROM_TRY(scratch_alloc((void **)&dout, sizeof(double) * nout, st));
-    PTROM_TRY(scratch_alloc((void **)&R, sizeof(double) * (size_t)nd * maxres, st));
+    PTROM_TRY(sc.alloc(&doff, sizeof(int) * (n + 1)));
+    PTROM_TRY(sc.alloc(&didx, sizeof(int) * std::max<size_t>(all.idx.size(), 1)));
+    PTROM_TRY(sc.alloc(&dout, sizeof(double) * nout));
+    PTROM_TRY(sc.alloc(&R, sizeof(double) * (size_t)nd * maxres));
     PTROM_CUDA(cudaMemcpyAsync(dphi, phif.data(), sizeof(float) * phif.size(), cudaMemcpyHostToDevice, st));
     PTROM_CUDA(cudaMemcpyAsync(doff, all.off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
     if (!all.idx.empty())
@@ -1195,9 +1200,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     inf.mean_list = (double)idx.size() / ns;
     inf.seconds_sample = secs(t0);
     // free the stage buffers
-    for (void *b : std::vector<void *>{S_own, x, f, work, dphi, dx0, dphic, dx0c, dgc, dxt, dpd, dxq, dxh, ddx, df, dfp,
-                                        dD, dr, dpart, du, doff, didx, dout, R})
-        if (b) PTROM_TRY(scratch_free(b, st));
+    PTROM_TRY(sc.release());
     PTROM_CUDA(cudaStreamSynchronize(st));
     PTROM_TRY(scratch_trim());  // hand the training buffers back to the device
     // ---------------- the online model
