@@ -49,8 +49,11 @@ WORKLOAD = {
     "gmres": "restart 30, rtol 1e-4, block-diagonal right preconditioner",
     "l2": "flushed (256 MB memset) before every timed step",
 }
-# Algorithmic FP32 flops per pair (an FMA counts 2, the reciprocal 1); the
-# derivation per kernel is in the design doc.
+# Algorithmic FP32 flops per pair (an FMA counts 2, the reciprocal 1), counted
+# from each operation's pair body: velocity = 2 differences + |r|^2 + delta
+# (2 FMA) + reciprocal + gamma r^-1 + 2 accumulating FMA = 12; the self blocks
+# add 12; J v = the velocity's first 8 + 2 differences of v + a dv_x + b dv_y
+# (3) + 2 products + 4 accumulating FMA = 23; J^T w with (df/dGamma)^T w = 31.
 FLOPS_PER_PAIR = {"velocity": 12, "velocity_selfjac": 24, "jvp": 23, "vjp": 31}
 
 
