@@ -668,12 +668,26 @@ def _e2e(args, ptrom, params, x0, G, dev, stream, n):
 
 
 def kernel_only(args):
-    """Launch one all-pairs kernel `args.steps` times at N = args.n (for ncu)."""
+    """Launch one all-pairs kernel `args.steps` times at N = args.n (for ncu);
+    with "ptrom", train the PTROM leg's model (theta 0.5, FP32 QR; untimed)
+    and launch the online kernel args.warmup + args.steps times, 10 time
+    steps per launch."""
     import torch
 
     from paper_2103_01983_gb300 import ptrom
     from paper_2103_01983_gb300 import workloads as W
 
+    if args.kernel_only == "ptrom":
+        x0, G = W.two_cluster(args.n, seed=0)
+        fp = ptrom.fom_params(WORKLOAD["dt"], WORKLOAD["delta"], "jfnk", tol=WORKLOAD["newton_tol"], prec="fp32c")
+        model, _ = ptrom.ptrom_build(torch.tensor(x0, device="cuda")[None], torch.tensor(G, device="cuda")[None],
+                                     20, 40, 40, 200, fp, criterion="bh", theta=0.5, qr_prec="fp32c")
+        st = model.new_state()
+        for _ in range(args.warmup + args.steps):
+            ptrom.ptrom_step([model], [st], 10, want_stats=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_only": "ptrom", "n": args.n, "launches": args.warmup + args.steps}))
+        return
     x0, G = W.two_cluster(args.n, seed=0)
     x = torch.tensor(x0, device="cuda")
     Gt = torch.tensor(G, device="cuda")
@@ -701,7 +715,7 @@ def main():
                     help="also run the paper's vortex-pair parametric experiment (about 3 minutes)")
     ap.add_argument("--mushroom", action="store_true",
                     help="also run the paper's mushroom-cloud parametric experiment (about 5 minutes)")
-    ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp"],
+    ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp", "ptrom"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")
     args = ap.parse_args()

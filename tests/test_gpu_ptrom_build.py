@@ -311,3 +311,15 @@ def test_caller_snapshots_give_the_same_model(P):
     np.testing.assert_array_equal(a["sampled"], b["sampled"])
     np.testing.assert_array_equal(a["A"], b["A"])
     assert info["n_snapshots"] == steps
+
+
+def test_build_errors_leave_the_library_usable(P):
+    """A build that fails after its training buffers are allocated (POD rank
+    above the snapshot count) returns EINVAL, and the next build succeeds."""
+    x0, G = W.two_cluster(256, seed=2)
+    fp = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c")
+    with pytest.raises(P.PtromError) as e:
+        P.ptrom_build(_dev(x0)[None], _dev(G)[None], 30, 40, 20, 20, fp, theta=0.5)
+    assert e.value.status == P.EINVAL
+    model, info = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 8, 16, 16, 20, fp, theta=0.5)
+    assert info["n_snapshots"] == 20 and model.M == 8
