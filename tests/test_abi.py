@@ -70,3 +70,41 @@ def test_model_file_errors_before_any_cuda_call(lib, tmp_path):
     short.write_bytes(b"PTROM")
     assert L.ptrom_load(str(short).encode(), ctypes.byref(h)) == -1
     assert "too short" in lib.last_error()
+
+
+_MIRRORS = {  # C struct -> binding class name
+    "ptrom_fom_params": "FomParams",
+    "ptrom_fom_stats": "FomStats",
+    "ptrom_model_desc": "ModelDesc",
+    "ptrom_stats": "PtromStats",
+    "ptrom_build_params": "BuildParams",
+    "ptrom_build_info": "BuildInfo",
+}
+
+
+def test_binding_structs_match_the_header_layout(lib, tmp_path):
+    """Every ctypes mirror has the C struct's size and every field its offset
+    (the header compiled as C99 with the host compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ptrom.h"', "int main(void) {"]
+    for cname, pyname in _MIRRORS.items():
+        cls = getattr(lib, pyname)
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    c = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    for cname, pyname in _MIRRORS.items():
+        cls = getattr(lib, pyname)
+        assert int(c[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(c[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
