@@ -50,6 +50,22 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert L.bs_vjp(1, null, null, 0.1, null, null, null, 0, null) == -1
     assert L.ptrom_set_source_split(9) == -1
     assert L.ptrom_set_source_split(0) == 0
+    assert L.ptrom_set_inflow(None, None) == -1
+    assert L.ptrom_set_inflow_full(None, None, None) == -1
+    assert L.ptrom_set_pod_exact_max(0) == -1
+    # the batched FOM takes no inflow: rejected before the instances are looked at
+    fp = lib.fom_params(0.01, 0.05, "blockdiag", prec="fp64")
+    fp.u_inf = 16
+    one = (ctypes.c_void_p * 1)(16)
+    n = (ctypes.c_int * 1)(4)
+    wb = (ctypes.c_size_t * 1)(1 << 20)
+    assert L.fom_step_batched(ctypes.byref(fp), 1, n, one, one, one, one, wb, None, None) == -1
+    assert "u_inf" in lib.last_error()
+    # ptrom_build: sizes are checked before any device work
+    bp = lib.BuildParams(8, 16, 16, 0, 0.5, 1.0, 10, 1e-4, 100, 1, lib.fom_params(0.01, 0.05, "jfnk"))
+    h = ctypes.c_void_p(0)
+    assert L.ptrom_build(ctypes.byref(bp), 1, 1, one, one, ctypes.byref(h), None, None) == -1
+    assert "sizes" in lib.last_error()
 
 
 def test_model_file_errors_before_any_cuda_call(lib, tmp_path):
