@@ -119,3 +119,28 @@ def test_mushroom_workload_matches_the_paper():
     train, query = W.mushroom_params(0)
     assert train.shape == (4, 2) and query.shape == (36, 2)
     assert np.all((train[:, 0] >= -220) & (train[:, 0] <= -110) & (train[:, 1] >= 110) & (train[:, 1] <= 220))
+
+
+def test_mae_d_and_ae_h_closed_forms():
+    """MAE_D (Eq. MAE_trajectory): every body displaced by the same vector d
+    gives |d| / l with l = |x_N^0 - x_1^0|; AE_H (Eq. AE_Hamiltonian) is the
+    relative gap of the Hamiltonians; a rigid translation leaves H unchanged."""
+    x0 = np.array([0.0, 3.0, 1.0, 0.0, 4.0, 2.0])          # bodies (0,0), (3,4), (1,2): l = |(1,2)| = sqrt 5
+    G = np.array([1.0, -2.0, 0.5])
+    d = np.array([0.3, -0.4])                              # |d| = 0.5
+    shifted = x0 + np.repeat(d, 3)
+    assert qoi.mae_d(x0, shifted, x0) == pytest.approx(0.5 / np.sqrt(5.0), rel=1e-15)
+    assert qoi.hamiltonian(shifted, G) == pytest.approx(qoi.hamiltonian(x0, G), rel=1e-14)
+    assert qoi.ae_h(1.1, 1.0) == pytest.approx(0.1, rel=1e-14)
+    # three-body H by hand: pairs (1,2) r = 5, (1,3) r = sqrt 5, (2,3) r = sqrt 8
+    h = (1.0 * -2.0 * np.log(5.0) + 1.0 * 0.5 * np.log(np.sqrt(5.0)) + -2.0 * 0.5 * np.log(np.sqrt(8.0))) / (2 * np.pi)
+    assert qoi.hamiltonian(x0, G) == pytest.approx(h, rel=1e-14)
+
+
+def test_impulses_closed_forms():
+    """Linear impulse P = sum Gamma_i x_i and angular impulse I = sum Gamma_i
+    |x_i|^2 on a hand-sized case."""
+    x = np.array([1.0, -2.0, 0.5, 3.0])                    # bodies (1, 0.5), (-2, 3)
+    G = np.array([2.0, -1.0])
+    np.testing.assert_array_equal(qoi.linear_impulse(x, G), [2.0 * 1.0 - 1.0 * -2.0, 2.0 * 0.5 - 1.0 * 3.0])
+    assert qoi.angular_impulse(x, G) == 2.0 * (1.0 + 0.25) - 1.0 * (4.0 + 9.0)
