@@ -317,9 +317,9 @@ def run_ours(args):
     if rank == 0 and not args.no_batch:
         line["batched"] = batch_leg(ptrom, dev)
     if rank == 0 and args.vortex_pair:
-        line["vortex_pair"] = vortex_pair_leg(ptrom, dev)
+        line["vortex_pair"] = vortex_pair_leg(ptrom, dev, args.qr_prec)
     if rank == 0 and args.mushroom:
-        line["mushroom"] = mushroom_leg(ptrom, dev)
+        line["mushroom"] = mushroom_leg(ptrom, dev, args.qr_prec)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
@@ -429,23 +429,24 @@ def ptrom_leg(ptrom, dev, fom_ms_per_step, steps=200):
     return out
 
 
-def vortex_pair_leg(ptrom, dev):
+def vortex_pair_leg(ptrom, dev, qr_prec="fp64"):
     """The paper's vortex-pair parametric experiment (Sec. 6.2); see
     ``parametric_leg``."""
-    return parametric_leg(ptrom, dev, "vortex_pair")
+    return parametric_leg(ptrom, dev, "vortex_pair", qr_prec)
 
 
-def mushroom_leg(ptrom, dev):
+def mushroom_leg(ptrom, dev, qr_prec="fp64"):
     """The paper's mushroom-cloud parametric experiment (Sec. 6.3, with the
     superimposed inflow); see ``parametric_leg``."""
-    return parametric_leg(ptrom, dev, "mushroom")
+    return parametric_leg(ptrom, dev, "mushroom", qr_prec)
 
 
-def parametric_leg(ptrom, dev, which):
+def parametric_leg(ptrom, dev, which, qr_prec="fp64"):
     """One of the paper's parametric experiments end to end: PTROM trained at
     4 Latin-hypercube parameters, queried on the 6 x 6 grid; time-averaged
     QoI errors against the GPU FOM at each query, and the PTROM-vs-FOM step
-    speed-up (GPU FOM step time / GPU PTROM step time)."""
+    speed-up (GPU FOM step time / GPU PTROM step time).  qr_prec: the online
+    least squares' precision (FP64 Householder QR, or FP32)."""
     import numpy as np
     import torch
 
@@ -460,7 +461,7 @@ def parametric_leg(ptrom, dev, which):
                  "paper_speedup_mean": 3.94}
         l = float(np.hypot(2 * V["half_width"], 2 * V["half_width"]))
         desc = ("vortex pair, N=500, delta=0.2121, dt=0.01, 500 steps; trained at 4 LHS parameters, "
-                "queried on the 6x6 grid; M=85, M_r=110, 60 sampled bodies, neighbour p_c=1, FP64 QR")
+                "queried on the 6x6 grid; M=85, M_r=110, 60 sampled bodies, neighbour p_c=1")
     else:
         V = W.MUSHROOM
         train, query = W.mushroom_params(0)
@@ -470,13 +471,13 @@ def parametric_leg(ptrom, dev, which):
                  "paper_speedup_mean": 1.71}
         l = 2 * V["half_width"]
         desc = ("mushroom cloud, N=500, delta=0.15, dt=0.005, 1000 steps, semicircular inflow; trained at 4 LHS "
-                "parameters, queried on the 6x6 grid; M=110, M_r=185, 75 sampled bodies, neighbour p_c=1, FP64 QR")
+                "parameters, queried on the 6x6 grid; M=110, M_r=185, 75 sampled bodies, neighbour p_c=1")
     n, delta, dt, steps = V["n"], V["delta"], V["dt"], V["steps"]
     fp = ptrom.fom_params(dt, delta, "jfnk", tol=1e-12, prec="fp64", gmres_rtol=1e-10, gmres_max_iter=400)
     xs, gs, us = zip(*[setup(a, b) for a, b in train])
     t0 = time.perf_counter()
     model, info = ptrom.ptrom_build(torch.tensor(np.stack(xs), device=dev), torch.tensor(np.stack(gs), device=dev),
-                                    M, Mr, ns, steps, fp, criterion="nb", p_c=1.0, tol=1e-4, qr_prec="fp64",
+                                    M, Mr, ns, steps, fp, criterion="nb", p_c=1.0, tol=1e-4, qr_prec=qr_prec,
                                     u_infs=None if us[0] is None else torch.tensor(np.stack(us), device=dev))
     build_s = time.perf_counter() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -514,7 +515,7 @@ def parametric_leg(ptrom, dev, which):
                              / abs(_hamiltonian_gpu(fom[k], Gd, n)) for k in ks]))
         rows.append((float(g1), float(gN), mae, aeh, fom_ms / rom_ms))
     r = np.array(rows)
-    return {"workload": desc, "build_s": build_s, "N_c": info["N_c"], "paper_N_c": paper["paper_N_c"],
+    return {"workload": desc, "qr_prec": qr_prec, "build_s": build_s, "N_c": info["N_c"], "paper_N_c": paper["paper_N_c"],
             "mae_d_mean": float(r[:, 2].mean()), "mae_d_max": float(r[:, 2].max()),
             "paper_mae_d_mean": paper["paper_mae_d_mean"],
             "ae_h_mean": float(r[:, 3].mean()), "ae_h_max": float(r[:, 3].max()),
@@ -715,6 +716,8 @@ def main():
                     help="also run the paper's vortex-pair parametric experiment (about 3 minutes)")
     ap.add_argument("--mushroom", action="store_true",
                     help="also run the paper's mushroom-cloud parametric experiment (about 5 minutes)")
+    ap.add_argument("--qr-prec", choices=["fp64", "fp32c"], default="fp64",
+                    help="online least-squares precision of the --vortex-pair / --mushroom legs")
     ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp", "ptrom"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")
