@@ -167,3 +167,23 @@ def test_exactness_without_clustering(P):
     rec = np.array([rom.reconstruct(z, Phi, x0) for z in hist.cpu().numpy()])
     err = np.abs(rec - traj[1:]).max() / np.abs(traj[1:] - x0).max()
     assert err <= 1e-4, err
+
+
+def test_one_launch_of_different_models(P):
+    """Instances of different models (sizes M = 8 / 16, n_s = 32 / 40,
+    different cluster counts, one with a superimposed inflow) share one
+    launch: every instance ends exactly where it ends when launched alone."""
+    ca, cb = _case("disk_bh"), _case("mushroom_bh")
+    ma, mb = _model(P, ca), _model(P, cb)
+    models = [ma, mb, ma, mb]
+    sts = [m.new_state() for m in models]
+    outs = [torch.zeros(m.M, dtype=torch.float64, device="cuda") for m in (ma, mb, ma, mb)]
+    s = P.ptrom_step(models, sts, 30, xhat=outs)
+    assert s["steps"] == 4 * 30
+    for m, o in ((ma, outs[0]), (mb, outs[1])):
+        st = m.new_state()
+        alone = torch.zeros(m.M, dtype=torch.float64, device="cuda")
+        P.ptrom_step([m], [st], 30, xhat=[alone])
+        np.testing.assert_array_equal(o.cpu().numpy(), alone.cpu().numpy())
+    np.testing.assert_array_equal(outs[0].cpu().numpy(), outs[2].cpu().numpy())
+    np.testing.assert_array_equal(outs[1].cpu().numpy(), outs[3].cpu().numpy())
