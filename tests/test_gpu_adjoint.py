@@ -94,10 +94,13 @@ def test_rollout_gradient_matches_central_differences(mods):
 
 
 @pytest.mark.parametrize("n,steps,every,prec,tol", [(1024, 40, 10, "fp64", 1e-9),
-                                                    (16384, 20, 10, "fp32c", 1e-5)])
+                                                    (16384, 20, 10, "fp32c", 1e-5),
+                                                    (65536, 100, 10, "fp32c", 1e-5)])
 def test_linear_impulse_gradient_closed_form(mods, n, steps, every, prec, tol):
     """L = sum Gamma_i (chi_i(T) + psi_i(T)) is conserved: dL/dx0 = Gamma on
-    both components and the total dL/dGamma = chi0 + psi0."""
+    both components and the total dL/dGamma = chi0 + psi0.  The largest case
+    is the full-size differentiation workload: N = 65536, the gradient of the
+    final linear impulse after 100 steps with a checkpoint every 10."""
     ptrom, ag = mods
     x0, G = W.two_cluster(n, seed=78)
     xt, Gt = _dev(x0, True), _dev(G, True)
