@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     objs = [o for o, _ in results]
     tmp = OUT + ".tmp"
     cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas",
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas", "-lcusolver",
            "-Xlinker", "-rpath", "-Xlinker", cudalib]
     subprocess.run(cmd, check=True)
     os.replace(tmp, OUT)

@@ -4,14 +4,15 @@
 // GPU: FOM training runs (fom_step), the FP64 snapshot Gram matrix and basis
 // products, and Tier-II LSPG over all bodies (cluster gather, warp-per-body
 // pair sums with the residual, normal equations of the Gauss-Newton least
-// squares).  Host C++: the symmetric eigen-solver of the Gram matrix
-// (tridiagonal + QL, symeig.h), the quadtree over the weighted POD space with WeightedMean,
+// squares), the symmetric eigen-solve of the Gram or covariance matrix
+// (cuSOLVER syevd).  Host C++: the quadtree over the weighted POD space with WeightedMean,
 // FindClusters/checkPrune and UniqueSearch (Alg. 2/3), the greedy sampling
 // (Alg. 1) and the gappy pseudo-inverse; their sizes are O(N) or tiny.
 #include <math.h>
 #include <string.h>
 
 #include <cublas_v2.h>
+#include <cusolverDn.h>
 
 #include <algorithm>
 #include <chrono>
@@ -24,7 +25,6 @@
 #include "internal.h"
 #include "ptrom_model.h"
 #include "scratch.h"
-#include "symeig.h"
 
 namespace ptrom {
 namespace {
@@ -575,6 +575,69 @@ static int cublas_for(cudaStream_t st, cublasHandle_t *out) {
     return PTROM_OK;
 }
 
+// A cuSOLVER dense handle per device (created on first use), bound to `st`.
+static int cusolver_for(cudaStream_t st, cusolverDnHandle_t *out) {
+    static std::mutex mu;
+    static cusolverDnHandle_t hs[64] = {};
+    int dev = 0;
+    PTROM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(PTROM_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!hs[dev] && cusolverDnCreate(&hs[dev]) != CUSOLVER_STATUS_SUCCESS)
+        return set_error(PTROM_ECUDA, "cusolverDnCreate failed");
+    if (cusolverDnSetStream(hs[dev], st) != CUSOLVER_STATUS_SUCCESS)
+        return set_error(PTROM_ECUDA, "cusolverDnSetStream failed");
+    *out = hs[dev];
+    return PTROM_OK;
+}
+
+// Eigen-decomposition of the symmetric n x n host matrix A (row-major, which
+// for a symmetric matrix is also its column-major form) by cuSOLVER's
+// divide-and-conquer syevd on the GPU, FP64.  On return w holds the
+// eigenvalues in descending order and V (n x n, row-major) the eigenvectors as
+// columns.  If the library reports a failure to converge, the host cyclic
+// Jacobi method above is used instead.
+static int sym_eig(cudaStream_t st, int n, const std::vector<double> &A, std::vector<double> &w,
+                   std::vector<double> &V) {
+    cusolverDnHandle_t h;
+    PTROM_TRY(cusolver_for(st, &h));
+    int lwork = 0;
+    if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, nullptr, n, nullptr,
+                                    &lwork) != CUSOLVER_STATUS_SUCCESS)
+        return set_error(PTROM_ECUDA, "cusolverDnDsyevd_bufferSize failed (n=%d)", n);
+    double *dA = nullptr, *dw = nullptr, *dwork = nullptr;
+    int *dinfo = nullptr;
+    ScratchScope sc(st);
+    PTROM_TRY(sc.alloc(&dA, sizeof(double) * (size_t)n * n));
+    PTROM_TRY(sc.alloc(&dw, sizeof(double) * (size_t)n));
+    PTROM_TRY(sc.alloc(&dwork, sizeof(double) * (size_t)std::max(lwork, 1)));
+    PTROM_TRY(sc.alloc(&dinfo, sizeof(int)));
+    PTROM_CUDA(cudaMemcpyAsync(dA, A.data(), sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice, st));
+    if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dw, dwork, lwork, dinfo) !=
+        CUSOLVER_STATUS_SUCCESS)
+        return set_error(PTROM_ECUDA, "cusolverDnDsyevd failed (n=%d)", n);
+    std::vector<double> ev((size_t)n * n), wa(n);
+    int info = 0;
+    PTROM_CUDA(cudaMemcpyAsync(ev.data(), dA, sizeof(double) * ev.size(), cudaMemcpyDeviceToHost, st));
+    PTROM_CUDA(cudaMemcpyAsync(wa.data(), dw, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    PTROM_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PTROM_CUDA(cudaStreamSynchronize(st));
+    PTROM_TRY(sc.release());
+    if (info != 0) {
+        jacobi_eig(n, A, w, V);
+        return PTROM_OK;
+    }
+    // syevd: ascending eigenvalues, eigenvector j in column j (column-major)
+    w.resize(n);
+    V.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        const int src = n - 1 - j;
+        w[j] = wa[src];
+        for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = ev[(size_t)src * n + i];
+    }
+    return PTROM_OK;
+}
+
 // Orthonormalise the m x r column-major device block A in place (SVQB: with
 // A^T A = V L V^T, A <- A V L^{-1/2}), dropping directions whose eigenvalue is
 // below 1e-20 of the largest; r may shrink.  T: m x r scratch.
@@ -584,7 +647,7 @@ static int svqb(cublasHandle_t h, int m, int &r, double *A, double *T, double *G
     std::vector<double> G((size_t)r * r), w, V;
     PTROM_CUDA(cudaMemcpyAsync(G.data(), Gd, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, st));
     PTROM_CUDA(cudaStreamSynchronize(st));
-    if (!symeig(r, G, w, V)) jacobi_eig(r, G, w, V);
+    PTROM_TRY(sym_eig(st, r, G, w, V));
     int keep = 0;
     while (keep < r && w[keep] > 1e-20 * w[0]) ++keep;
     if (keep == 0) return set_error(PTROM_EINVAL, "ptrom_build: POD range block has rank 0");
@@ -641,7 +704,7 @@ static int pod_randomized(int nd, int K, const double *S, int &M, cudaStream_t s
     std::vector<double> G((size_t)r * r), w, V;
     PTROM_CUDA(cudaMemcpyAsync(G.data(), Gd, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, st));
     PTROM_CUDA(cudaStreamSynchronize(st));
-    if (!symeig(r, G, w, V)) jacobi_eig(r, G, w, V);
+    PTROM_TRY(sym_eig(st, r, G, w, V));
     if (clamp) {
         int q = 0;
         while (q < M && q < r && w[q] > 1e-24 * w[0]) ++q;
@@ -697,7 +760,7 @@ int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vec
         for (int a = 0; a < nd; ++a)
             for (int b = 0; b < a; ++b) Ch[(size_t)a * nd + b] = Ch[(size_t)b * nd + a];
         std::vector<double> w, V;
-        if (!symeig(nd, Ch, w, V)) jacobi_eig(nd, Ch, w, V);
+        PTROM_TRY(sym_eig(st, nd, Ch, w, V));
         if (clamp) {
             int r = 0;
             while (r < M && w[r] > 1e-24 * w[0]) ++r;
@@ -732,7 +795,7 @@ int pod_device(int nd, int K, const double *S, int &M, cudaStream_t st, std::vec
     for (int a = 0; a < K; ++a)
         for (int b = 0; b < a; ++b) Gh[(size_t)a * K + b] = Gh[(size_t)b * K + a];
     std::vector<double> w, V;
-    if (!symeig(K, Gh, w, V)) jacobi_eig(K, Gh, w, V);  // Jacobi as the slow, always-convergent fallback
+    PTROM_TRY(sym_eig(st, K, Gh, w, V));
     if (clamp) {
         int r = 0;
         while (r < M && w[r] > 1e-24 * w[0]) ++r;
