@@ -55,11 +55,26 @@ int ptrom_last_error(char *buf, size_t len);
 /* Library version (major*10000 + minor*100 + patch). */
 int ptrom_version(void);
 
-/* Tuning override for the all-pairs kernels: split every launch's sources
- * over S CTAs of one thread-block cluster (1 <= S <= 8), or S = 0 to restore
- * the automatic choice (the default).  Process-wide; results are identical up
- * to FP rounding for every S.  Returns PTROM_EINVAL for S outside [0, 8]. */
+/* Tuning overrides for the all-pairs kernels (process-wide; results are
+ * identical up to FP rounding for every choice, and each choice is
+ * deterministic run to run).
+ * ptrom_set_source_split(S): split every launch's sources over S CTAs per
+ *   block of 64 targets (1 <= S <= 16; at most 8 with the cluster combine), or
+ *   S = 0 to restore the automatic choice (the default).  Returns PTROM_EINVAL
+ *   for S outside [0, 16]; a launch whose combine cannot take the forced S
+ *   returns PTROM_EINVAL.
+ * ptrom_set_split_mode(mode): how the S partial sums of a target block are
+ *   added, both in a fixed split order:
+ *     0  automatic (the default): global, unless a caller-supplied scratch
+ *        holds the packed sources only (then cluster);
+ *     1  cluster: the S CTAs form a thread-block cluster and add their
+ *        partials through distributed shared memory (no scratch, S <= 8);
+ *     2  global: each CTA writes its partial to scratch and the last to
+ *        arrive adds them (S <= 16; PTROM_ENOMEM if a caller's scratch is too
+ *        small).
+ *   Returns PTROM_EINVAL for mode outside [0, 2]. */
 int ptrom_set_source_split(int S);
+int ptrom_set_split_mode(int mode);
 
 /* Instrumentation (host-side, process-wide).
  * ptrom_launch_count: number of CUDA kernels the library has launched so far.
@@ -126,8 +141,9 @@ int bs_velocity(int nt, const double *xt, int ns, const double *xs,
  * Notes: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  All calls share the one array and it keeps the last
- * call's contents (every record a call reads is rewritten by that call first,
- * so nothing needs clearing); calls that overlap on the GPU -- on different
+ * call's contents (every record a call reads, and every arrival counter of its
+ * source split's combine, is rewritten by that call first, so nothing needs
+ * clearing); calls that overlap on the GPU -- on different
  * streams, or from different host threads -- race on it and must be ordered
  * by the caller.
  */

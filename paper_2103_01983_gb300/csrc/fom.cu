@@ -850,6 +850,7 @@ struct Work {
     double *Mi;    // [4][n] preconditioner blocks (M_i^{-1})
     GmDev gm;
     void *pack;
+    size_t pack_bytes;
     unsigned int *counter;
     int *flags;    // flags[0]: skip the queued Newton-update kernels
     int *perm, *status;
@@ -901,7 +902,8 @@ static Work layout(const ptrom_fom_params *p, int n, char *base) {
     W.gm.sn = (double *)take(sizeof(double) * kMaxRestart);
     W.gm.g = (double *)take(sizeof(double) * (kMaxRestart + 1));
     W.gm.scal = (double *)take(sizeof(double) * 2);
-    W.pack = take(pack_scratch_bytes(n));
+    W.pack_bytes = pack_scratch_bytes(n, n);
+    W.pack = take(W.pack_bytes);
     if (p->jac_mode == PTROM_JAC_DENSE) {
         W.M = (double *)take(n2 * n2 * 8);
         W.perm = (int *)take(n2 * 4);
@@ -1014,6 +1016,7 @@ static int apply_jvp(Ctx &c, const double *v, double *out, bool lin, const int *
                      Slots *slots = nullptr) {
     LaunchOpts o;
     o.scratch = c.W.pack;
+    o.scratch_bytes = c.W.pack_bytes;
     o.skip = skip;
     o.slots = slots;
     if (lin) {
@@ -1255,6 +1258,7 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
         const bool refresh = (k % p->p_it == 0) || !have_jac;
         LaunchOpts vo;
         vo.scratch = W.pack;
+        vo.scratch_bytes = W.pack_bytes;
         PTROM_TRY(velocity(n, x, n, x, Gamma, p->delta, W.fxi, refresh ? W.D : nullptr, p->prec, c.st, vo));
         c.stats->velocity_evals++;
         const bool jfnk = p->jac_mode == PTROM_JAC_JFNK;
@@ -1394,6 +1398,7 @@ extern "C" int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *
     // self blocks at x^n for the (transposed) preconditioner
     LaunchOpts po;
     po.scratch = W.pack;
+    po.scratch_bytes = W.pack_bytes;
     PTROM_TRY(velocity(n, x_n, n, x_n, Gamma, q.delta, W.fxi, W.D, q.prec, c.st, po));
     c.stats->velocity_evals++;
     k_minv<<<c.grid, 256, 0, c.st>>>(n, W.D, c.hdt, W.Mi);

@@ -15,8 +15,11 @@ struct LinEpi {
 
 // Options of one all-pairs launch (bs_pair.cu):
 //   split   0 -> automatic cluster split, S in 1..8 -> forced;
-//   scratch device buffer of at least pack_scratch_bytes(ns) bytes for the
-//           packed sources, or nullptr (stream-ordered allocation from the pool);
+//   scratch device buffer for the packed sources and the split's partial
+//           sums, of scratch_bytes bytes (pack_scratch_bytes(nt, ns) bytes
+//           always suffice; one that holds the records only makes the launch
+//           combine its split through a thread-block cluster), or nullptr
+//           (stream-ordered allocation from the pool);
 //   lin     J v / J^T w only: the (I - hdt J) epilogue;
 //   skip    optional device flag: nonzero at launch -> the launch does nothing;
 //   slots   optional: collects the launches' timing slots (so a launch that
@@ -31,6 +34,7 @@ struct Slots {
 struct LaunchOpts {
     int split = 0;
     void *scratch = nullptr;
+    size_t scratch_bytes = 0;
     LinEpi lin;
     const int *skip = nullptr;
     Slots *slots = nullptr;
@@ -42,7 +46,11 @@ int jvp(int n, const double *x, const double *G, double delta, const double *v, 
         int prec, cudaStream_t st, const LaunchOpts &o = {});
 int vjp(int n, const double *x, const double *G, double delta, const double *w, double *gx,
         double *gG, int prec, cudaStream_t st, const LaunchOpts &o = {});
-size_t pack_scratch_bytes(int ns);
+size_t pack_scratch_bytes(int nt, int ns);
+// Bytes per source that bs_velocity_noalloc's fixed scratch reserves: the
+// largest packed record of any velocity kernel (checked at compile time in
+// bs_pair.cu against every VelOp record).
+constexpr size_t kNoAllocRecordBytes = 48;
 // Batched velocity (+ self blocks when D != nullptr) over B instances; S = source split.
 int velocity_batched(int B, const int *n, const double *const *x, const double *const *G, const double *delta,
                      double *const *f, double *const *D, int prec, cudaStream_t st, int S);

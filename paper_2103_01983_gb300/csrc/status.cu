@@ -57,8 +57,18 @@ std::atomic<int> g_source_split{0};
 }
 
 extern "C" int ptrom_set_source_split(int S) {
-    if (S < 0 || S > 8) return ptrom::set_error(PTROM_EINVAL, "ptrom_set_source_split: S=%d outside [0, 8]", S);
+    if (S < 0 || S > 16) return ptrom::set_error(PTROM_EINVAL, "ptrom_set_source_split: S=%d outside [0, 16]", S);
     ptrom::g_source_split.store(S);
+    return PTROM_OK;
+}
+
+namespace ptrom {
+std::atomic<int> g_split_mode{0};
+}
+
+extern "C" int ptrom_set_split_mode(int mode) {
+    if (mode < 0 || mode > 2) return ptrom::set_error(PTROM_EINVAL, "ptrom_set_split_mode: mode=%d outside [0, 2]", mode);
+    ptrom::g_split_mode.store(mode);
     return PTROM_OK;
 }
 

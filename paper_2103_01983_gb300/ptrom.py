@@ -110,6 +110,7 @@ def _load():
         "ptrom_last_error": ([ctypes.c_char_p, ctypes.c_size_t], _i),
         "ptrom_version": ([], _i),
         "ptrom_set_source_split": ([_i], _i),
+        "ptrom_set_split_mode": ([_i], _i),
         "bs_velocity": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_velocity_noalloc": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_jvp": ([_i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
@@ -224,8 +225,13 @@ def set_pod_exact_max(n: int) -> None:
 
 
 def set_source_split(S: int) -> None:
-    """Force the all-pairs kernels' cluster source split (0 = automatic)."""
+    """Force the all-pairs kernels' source split (1..16; 0 = automatic)."""
     _check(lib.ptrom_set_source_split(int(S)))
+
+
+def set_split_mode(mode: int) -> None:
+    """0 = automatic, 1 = thread-block-cluster combine, 2 = global combine."""
+    _check(lib.ptrom_set_split_mode(int(mode)))
 
 
 def bs_velocity(xs, Gamma, delta, xt=None, f_out=None, selfjac=False, prec="fp32c", stream=None):

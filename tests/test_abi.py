@@ -48,7 +48,9 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert L.bs_velocity(4, null, 4, null, null, 0.1, null, null, 0, null) == -1   # NULL arrays
     assert L.bs_jvp(1, null, null, 0.1, null, null, 0, null) == -1
     assert L.bs_vjp(1, null, null, 0.1, null, null, null, 0, null) == -1
-    assert L.ptrom_set_source_split(9) == -1
+    assert L.ptrom_set_source_split(17) == -1
+    assert L.ptrom_set_split_mode(3) == -1
+    assert L.ptrom_set_split_mode(0) == 0
     assert L.ptrom_set_source_split(0) == 0
     assert L.ptrom_set_inflow(None, None) == -1
     assert L.ptrom_set_inflow_full(None, None, None) == -1

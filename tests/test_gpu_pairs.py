@@ -1,9 +1,9 @@
 """Parity of the CUDA all-pairs kernels with the FP64 oracle (GPU).
 
 Tolerance: relative L2 error <= 1e-5 for the FP32-compensated path (the
-velocity-field bound of the benchmark spec, applied to every pair product),
-<= 1e-12 for the FP64 path.  Sizes span several 64-target tiles and
-32-source chunks with ragged tails, every cluster split 1..8, delta = 0
+velocity-field bound, applied to every pair product), <= 1e-12 for the FP64
+path.  Sizes span several 64-target tiles and 32-source chunks with ragged
+tails, source splits 1..16 with both combines, delta = 0
 (masked self pairs), distinct targets, and full-size spot checks.
 """
 import numpy as np
@@ -65,18 +65,26 @@ def test_velocity_and_selfjac(P, prec, n, delta, gen):
     assert _rel(D.cpu().numpy(), Do) <= TOL[prec]
 
 
-@pytest.mark.parametrize("split", [1, 2, 3, 5, 8])
-def test_every_cluster_split(P, split):
-    x, G = W.two_cluster(1536, seed=23)
+@pytest.mark.parametrize("mode,split", [(1, 1), (1, 2), (1, 3), (1, 5), (1, 8),
+                                        (2, 2), (2, 3), (2, 7), (2, 11), (2, 16), (0, 0)])
+def test_every_source_split_and_combine(P, mode, split):
+    """Cluster (mode 1) and global (mode 2) combines of the source split, and
+    the automatic choice; N = 1530 leaves a ragged last target block and a
+    ragged last chunk, and S = 16 gives some CTAs no chunk at all."""
+    x, G = W.two_cluster(1530, seed=23)
     fo, Do = direct.velocity(x, G, 0.02, with_selfjac=True)
+    P.set_split_mode(mode)
     P.set_source_split(split)
     try:
         f, D = P.bs_velocity(_dev(x), _dev(G), 0.02, selfjac=True)
         v = W.random_vectors(x.size, 1, seed=24)[0]
         jv = P.bs_jvp(_dev(x), _dev(G), 0.02, _dev(v))
         gx, gG = P.bs_vjp(_dev(x), _dev(G), 0.02, _dev(v))
+        jv2 = P.bs_jvp(_dev(x), _dev(G), 0.02, _dev(v))
     finally:
         P.set_source_split(0)
+        P.set_split_mode(0)
+    assert torch.equal(jv, jv2)  # the fixed-order combine is deterministic
     assert _rel(f.cpu().numpy(), fo) <= 1e-5
     assert _rel(D.cpu().numpy(), Do) <= 1e-5
     assert _rel(jv.cpu().numpy(), direct.jvp(x, G, 0.02, v)) <= 1e-5
@@ -85,9 +93,12 @@ def test_every_cluster_split(P, split):
     assert _rel(gG.cpu().numpy(), gGo) <= 1e-5
 
 
-def test_distinct_targets_grid(P):
+@pytest.mark.parametrize("ny", [29, 893])
+def test_distinct_targets_grid(P, ny):
+    """Grid targets; 37 x 893 = 33041 targets take the 4-set velocity kernel
+    (ragged last 256-target block)."""
     x, G = W.disk(900, seed=25)
-    gx, gy = np.meshgrid(np.linspace(-1.2, 1.2, 37), np.linspace(-1.1, 1.1, 29))
+    gx, gy = np.meshgrid(np.linspace(-1.2, 1.2, 37), np.linspace(-1.1, 1.1, ny))
     t = np.concatenate([gx.ravel(), gy.ravel()])
     fo = direct.velocity(x, G, 0.05, targets=t)
     f = P.bs_velocity(_dev(x), _dev(G), 0.05, xt=_dev(t)).cpu().numpy()
@@ -154,6 +165,8 @@ def test_full_size_sampled_rows(P, n):
     fo, Do = direct.velocity(x, G, delta, targets=x[idx], with_selfjac=True)
     assert _rel(f.cpu().numpy()[idx], fo) <= 1e-5
     assert _rel(D.cpu().numpy()[:, rows], Do) <= 1e-5
+    f1 = P.bs_velocity(_dev(x), _dev(G), delta).cpu().numpy()  # velocity alone (4 target sets at N >= 32768)
+    assert _rel(f1[idx], fo) <= 1e-5
     jv = P.bs_jvp(_dev(x), _dev(G), delta, _dev(v)).cpu().numpy()
     assert _rel(jv[idx], direct.jvp(x, G, delta, v, rows=rows)) <= 1e-5
     gx, gG = P.bs_vjp(_dev(x), _dev(G), delta, _dev(w))
