@@ -19,9 +19,9 @@ namespace ptrom {
 namespace {
 
 constexpr int kNoAllocMaxSources = PTROM_NOALLOC_MAX_SOURCES;
-// Largest packed-source record the velocity kernels use: the FP64 one, three
-// 16-byte pairs (FP32 records are 32 bytes).
-constexpr size_t kNoAllocRecordBytes = 48;
+// kNoAllocRecordBytes (internal.h): the largest packed-source record of the
+// velocity kernels, the FP64 one (three 16-byte pairs; FP32 records are 32
+// bytes), tied to the records' sizes by static_asserts in bs_pair.cu.
 constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxSources * kNoAllocRecordBytes;
 
 // The shared scratch.  In host code this name is only a stand-in for the
@@ -69,9 +69,13 @@ extern "C" int bs_velocity_noalloc(int nt, const double *xt, int ns, const doubl
     void *scratch = nullptr;
     PTROM_TRY(noalloc_scratch(&scratch));
     // The pack kernel rewrites every record the pair kernel reads (all
-    // ceil(ns/32)*32 of them, padding included) before it is read, so nothing
-    // in the array needs clearing between calls.
+    // ceil(ns/32)*32 of them, padding included) before it is read, and, when
+    // the rest of the array holds the split's partial sums, zeroes their
+    // arrival counters; so nothing in the array needs clearing between calls.
+    // When the partials do not fit beside the records, the launch combines its
+    // source split through a thread-block cluster instead.
     LaunchOpts o;
     o.scratch = scratch;
+    o.scratch_bytes = kNoAllocBytes;
     return velocity(nt, xt, ns, xs, Gamma, delta, f_out, selfjac_out, prec, (cudaStream_t)stream, o);
 }
