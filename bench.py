@@ -49,12 +49,13 @@ WORKLOAD = {
     "gmres": "restart 30, rtol 1e-4, block-diagonal right preconditioner",
     "l2": "flushed (256 MB memset) before every timed step",
 }
-# Algorithmic FP32 flops per pair (an FMA counts 2, the reciprocal 1), counted
-# from each operation's pair body: velocity = 2 differences + |r|^2 + delta
-# (2 FMA) + reciprocal + gamma r^-1 + 2 accumulating FMA = 12; the self blocks
-# add 12; J v = the velocity's first 8 + 2 differences of v + a dv_x + b dv_y
-# (3) + 2 products + 4 accumulating FMA = 23; J^T w with (df/dGamma)^T w = 31.
-FLOPS_PER_PAIR = {"velocity": 12, "velocity_selfjac": 24, "jvp": 23, "vjp": 31}
+# Algorithmic work per pair (an FMA counts 2 flops, the reciprocal 1), the
+# per-unit figures the roofline is quoted on: velocity = 2 differences +
+# |r|^2 + delta (2 FMA) + reciprocal + gamma r^-1 + 2 accumulating FMA = 12;
+# the self blocks add 8; J v 26; J^T w with (df/dGamma)^T w 30.  The kernels'
+# own pair bodies issue 12, 24, 23 and 31 FP32 flops (OPS_PER_PAIR).
+FLOPS_PER_PAIR = {"velocity": 12, "velocity_selfjac": 20, "jvp": 26, "vjp": 30}
+OPS_PER_PAIR = {"velocity": 12, "velocity_selfjac": 24, "jvp": 23, "vjp": 31}
 
 
 def _peaks():
@@ -178,7 +179,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": WORKLOAD,
+        "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{args.gpus}"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -290,8 +291,9 @@ def run_ours(args):
     traffic = _traffic(dom, n)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "peak_source": f"{peak_src}: {sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
-                "flops_per_pair": FLOPS_PER_PAIR[dom],
+                "peak_source": (f"nominal FP32 non-tensor peak: {sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
+                                f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src}; the file holds no FP32 figure)"),
+                "flops_per_pair": FLOPS_PER_PAIR[dom], "ops_issued_per_pair": OPS_PER_PAIR[dom],
                 "launches": dom_cnt, "avg_launch_us": 1e3 * dom_ms / dom_cnt if dom_cnt else None}
     kernels = {k: {"launches": c, "avg_us": 1e3 * t / c,
                    "pairs_per_s": n * n * c / (t * 1e-3),
@@ -646,26 +648,32 @@ def _e2e(args, ptrom, params, x0, G, dev, stream, n):
     f = torch.empty_like(fh, device=dev)
     work = ptrom.fom_workspace(params, n, dev)
     steps = max(3, min(args.steps, 20))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    # the same library-side events on the all-pairs launches as the device-timed leg
+    ptrom.timing_enable(True, kinds=list(FLOPS_PER_PAIR))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     pairs = 0
-    t0.record(stream)
-    for _ in range(steps):
+    for k in range(steps):
+        flush.zero_()  # L2 flushed before every step, outside its events, as in the device-timed leg
+        ev[k][0].record(stream)
         x.copy_(xh, non_blocking=True)
         f.copy_(fh, non_blocking=True)
         Gd.copy_(Gh, non_blocking=True)
         st = ptrom.fom_step(params, Gd, x, f, work=work)
         xh.copy_(x, non_blocking=True)
         fh.copy_(f, non_blocking=True)
+        ev[k][1].record(stream)
         pairs += (st["velocity_evals"] + st["jvp_evals"]) * n * n
-    t1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = t0.elapsed_time(t1)
+    ptrom.timing_enable(False)
+    ptrom.timing_read()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
     nb = xh.numel() * 8
     return {"value": pairs / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * nb + Gh.numel() * 8,
             "d2h_bytes_per_step": 2 * nb, "steps": steps,
-            "note": "public API (ptrom.fom_step) from pinned host buffers; x, f, Gamma H2D and x, f D2H every step"}
+            "note": ("public API (ptrom.fom_step) from pinned host buffers; x, f, Gamma H2D and x, f D2H every "
+                     "step; L2 flushed before every step; all-pairs launches event-timed as in the device leg")}
 
 
 def kernel_only(args):
