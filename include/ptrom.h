@@ -462,6 +462,49 @@ int ptrom_set_inflow_full(ptrom_model *m, const double *u, ptrom_stream_t stream
 int ptrom_reconstruct(const ptrom_model *m, const double *xhat, const int *rows,
                       int nrows, double *out, ptrom_stream_t stream);
 
+/* Training data of a model made by ptrom_build in this process (a model
+ * read by ptrom_load has none), for inspection and tests; any pointer may be
+ * NULL.  M_r, n_params, steps: the residual basis size, the training
+ * parameters and the time steps of each.  phi_r [2n x M_r] (HOST, row-major):
+ * the residual POD basis of Stage 3b, on which Alg. 1 sampled.  tier2_xhat
+ * [n_params x (steps + 1) x M] (HOST): the Tier-II LSPG reduced trajectory of
+ * every training parameter (Stage 3), from xhat = 0.  PTROM_EINVAL for other
+ * models. */
+int ptrom_model_query_training(const ptrom_model *m, int *M_r, int *n_params, int *steps,
+                               double *phi_r, double *tier2_xhat);
+
+/* The online model's clusters, for inspection and tests; any pointer may be
+ * NULL, and a first call with only the sizes tells how large the arrays are.
+ * N_c clusters; list_off [n_s + 1], list_idx [n_list] (HOST): sampled body s
+ * interacts with clusters list_idx[list_off[s] .. list_off[s+1]-1]; mem_off
+ * [N_c + 1], mem [n_members] (HOST): cluster c's member bodies (models made by
+ * ptrom_build or read by ptrom_load from one; PTROM_EINVAL otherwise);
+ * phi_c [2 N_c x M] (row-major, chi rows then psi rows), x0_c [2 N_c],
+ * gamma_c [N_c] (HOST): the clusters' POD surrogates, reference positions and
+ * circulations (Def. 1) for the model's current parameter. */
+int ptrom_model_query_clusters(const ptrom_model *m, int *N_c, int *n_list, int *n_members,
+                               int *list_off, int *list_idx, int *mem_off, int *mem,
+                               double *phi_c, double *x0_c, double *gamma_c);
+
+/* Alg. 1 greedy sampling of bodies, on the host (no CUDA call).
+ * phi_r [2n x M_r] (HOST, row-major: rows chi_1..chi_n, psi_1..psi_n), the
+ * residual basis; sampled [n_s] (HOST, out): body ids in the order chosen.
+ * Readings of the garbled counters: n_c = min(M_r, 2 n_s), n_it = min(n_c,
+ * n_s), iteration i takes n_ci = floor(n_c/n_it) + [i <= n_c mod n_it] more
+ * columns and n_ai = floor(n_s/n_it) + [i <= n_s mod n_it] bodies; from i = 2
+ * on, the new columns minus their minimum-norm gappy fit by the earlier
+ * columns on the chosen bodies' dofs; a body's error is the squared norm of
+ * its two rows; ties go to the lowest body id.  ptrom_build runs the same
+ * code.  PTROM_EINVAL for n < 1, M_r < 1, n_s outside [1, n] or NULL arrays. */
+int ptrom_greedy_sample(int n, int M_r, const double *phi_r, int n_s, int *sampled);
+
+/* The gappy operator A = [P Phi_r]^+ (Eq. gappySolution; the Moore-Penrose
+ * inverse, so the minimum-norm right inverse when 2 n_s < M_r), on the host
+ * (no CUDA call): phi_r as above, sampled [n_s] (HOST), A [M_r x 2 n_s]
+ * (HOST, out, row-major; columns chi of the sampled bodies, then psi).
+ * PTROM_EINVAL for bad sizes, NULL arrays or a body id outside [0, n). */
+int ptrom_gappy_operator(int n, int M_r, const double *phi_r, int n_s, const int *sampled, double *A);
+
 /* Host copies of a built model's offline data, for inspection and tests:
  * any pointer may be NULL.  phi [2n x M] row-major, sigma [M],
  * sampled [n_s] (body ids in Alg. 1 order), A [M_r x 2 n_s] row-major. */

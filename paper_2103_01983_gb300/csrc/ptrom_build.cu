@@ -120,6 +120,107 @@ bool lstsq_qr(int m, int n, std::vector<double> A, std::vector<double> B, int k,
     return true;
 }
 
+// Minimum-norm least squares X = argmin ||X|| over argmin ||A X - B|| (the
+// Moore-Penrose solution A^+ B) for any shape and rank (A: m x n col-major,
+// B: m x k col-major; X: n x k col-major).  A well-conditioned full-column-rank
+// A (m >= n) takes the Householder QR above, whose solution is then the unique
+// one; otherwise A's SVD is formed by one-sided Jacobi rotations (Hestenes:
+// rotate pairs of columns of A V until they are orthogonal, so A V = U Sigma),
+// and X = V Sigma^+ U^T B keeps the singular values above
+// max(m, n) * eps * sigma_max, the rank threshold of LAPACK-style least
+// squares drivers.
+void lstsq_minnorm(int m, int n, const std::vector<double> &A, const std::vector<double> &B, int k,
+                   std::vector<double> &X) {
+    if (m >= n) {
+        // QR fast path, taken only when the diagonal of R shows a well-conditioned A
+        bool ok = true;
+        double dmax = 0.0, dmin = INFINITY;
+        {
+            std::vector<double> T = A;
+            for (int j = 0; j < n && ok; ++j) {
+                double *cj = &T[(size_t)j * m];
+                double s2 = 0.0;
+                for (int i = j; i < m; ++i) s2 += cj[i] * cj[i];
+                const double nrm = sqrt(s2);
+                dmax = std::max(dmax, nrm);
+                dmin = std::min(dmin, nrm);
+                if (nrm == 0.0) {
+                    ok = false;
+                    break;
+                }
+                const double alpha = cj[j] >= 0 ? -nrm : nrm;
+                const double v0 = cj[j] - alpha;
+                const double vn2 = s2 - cj[j] * cj[j] + v0 * v0;
+                cj[j] = v0;
+                const double tau = vn2 > 0 ? 2.0 / vn2 : 0.0;
+                for (int c = j + 1; c < n; ++c) {
+                    double *col = &T[(size_t)c * m];
+                    double w = 0.0;
+                    for (int i = j; i < m; ++i) w += cj[i] * col[i];
+                    w *= tau;
+                    for (int i = j; i < m; ++i) col[i] -= w * cj[i];
+                }
+            }
+        }
+        if (ok && dmin > 1e-7 * dmax && lstsq_qr(m, n, A, B, k, X)) return;
+    }
+    // one-sided Jacobi SVD of A (m x n): columns of U S in Us, V (n x n)
+    std::vector<double> Us = A, V((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) V[(size_t)j * n + j] = 1.0;
+    const double eps = 2.220446049250313e-16;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double *up = &Us[(size_t)p * m], *uq = &Us[(size_t)q * m];
+                double alpha = 0.0, beta = 0.0, gamma = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    alpha += up[i] * up[i];
+                    beta += uq[i] * uq[i];
+                    gamma += up[i] * uq[i];
+                }
+                if (gamma == 0.0 || fabs(gamma) <= eps * sqrt(alpha * beta)) continue;
+                rotated = true;
+                const double zeta = (beta - alpha) / (2.0 * gamma);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int i = 0; i < m; ++i) {
+                    const double a = up[i], b = uq[i];
+                    up[i] = c * a - s * b;
+                    uq[i] = s * a + c * b;
+                }
+                double *vp = &V[(size_t)p * n], *vq = &V[(size_t)q * n];
+                for (int i = 0; i < n; ++i) {
+                    const double a = vp[i], b = vq[i];
+                    vp[i] = c * a - s * b;
+                    vq[i] = s * a + c * b;
+                }
+            }
+        }
+        if (!rotated) break;
+    }
+    std::vector<double> sv(n);
+    double smax = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s2 = 0.0;
+        for (int i = 0; i < m; ++i) s2 += Us[(size_t)j * m + i] * Us[(size_t)j * m + i];
+        sv[j] = sqrt(s2);
+        smax = std::max(smax, sv[j]);
+    }
+    const double cut = (double)std::max(m, n) * eps * smax;
+    X.assign((size_t)n * k, 0.0);
+    for (int j = 0; j < n; ++j) {
+        if (!(sv[j] > cut)) continue;
+        const double inv2 = 1.0 / (sv[j] * sv[j]);  // (U S)_j^T b / s_j^2 = U_j^T b / s_j
+        for (int c = 0; c < k; ++c) {
+            double w = 0.0;
+            for (int i = 0; i < m; ++i) w += Us[(size_t)j * m + i] * B[(size_t)c * m + i];
+            w *= inv2;
+            for (int i = 0; i < n; ++i) X[(size_t)c * n + i] += w * V[(size_t)j * n + i];
+        }
+    }
+}
+
 // Cholesky solve of G x = b (G n x n row-major, SPD); b is overwritten by x.
 bool chol_solve(int n, std::vector<double> G, std::vector<double> &b) {
     for (int j = 0; j < n; ++j) {
@@ -872,15 +973,17 @@ std::vector<int> greedy_sample(const std::vector<double> &Pr, int n, int Mr, int
                     for (int q = 0; q < n_ci; ++q) B[(size_t)q * m + ri] = R[(size_t)q * 2 * n + rows[h]];
                 }
             }
-            // rows ordered (chi, psi) per body here; the least-squares solution does not depend on row order
-            if (lstsq_qr(m, n_b, A, B, n_ci, X)) {
-                for (int q = 0; q < n_ci; ++q)
-                    for (int d = 0; d < 2 * n; ++d) {
-                        double s = 0.0;
-                        for (int c = 0; c < n_b; ++c) s += Pr[(size_t)d * Mr + c] * X[(size_t)q * n_b + c];
-                        R[(size_t)q * 2 * n + d] -= s;
-                    }
-            }
+            // rows ordered (chi, psi) per body here; the least-squares solution does not depend on row order.
+            // The minimum-norm solution: the gappy fit on few sampled dofs is
+            // under-determined or rank deficient when fewer dofs than columns
+            // are sampled or the columns coincide there.
+            lstsq_minnorm(m, n_b, A, B, n_ci, X);
+            for (int q = 0; q < n_ci; ++q)
+                for (int d = 0; d < 2 * n; ++d) {
+                    double s = 0.0;
+                    for (int c = 0; c < n_b; ++c) s += Pr[(size_t)d * Mr + c] * X[(size_t)q * n_b + c];
+                    R[(size_t)q * 2 * n + d] -= s;
+                }
         }
         for (int l = 0; l < n; ++l) {
             double e = 0.0;
@@ -901,6 +1004,27 @@ std::vector<int> greedy_sample(const std::vector<double> &Pr, int n, int Mr, int
         n_b += n_ci;
     }
     return chosen;
+}
+
+// A = [P Phi_r]^+ (Moore-Penrose, Eq. gappySolution): Ah [M_r][2 n_s]
+// row-major, P picking both dofs (chi rows, then psi rows) of each sampled
+// body.  P Phi_r is n_d x M_r; with n_d >= M_r and full column rank A is its
+// left inverse; with n_d < M_r (the gappy problem under-determined, as in the
+// paper's mushroom cloud, n_d = 150 < M_r = 185) the minimum-norm right inverse.
+void gappy_operator(const std::vector<double> &Pr, int n, int Mr, const std::vector<int> &sampled,
+                    std::vector<double> &Ah) {
+    const int ns = (int)sampled.size(), m2 = 2 * ns;
+    std::vector<double> PP((size_t)m2 * Mr), Iden((size_t)m2 * m2, 0.0), X;
+    for (int s = 0; s < ns; ++s)
+        for (int c = 0; c < Mr; ++c) {
+            PP[(size_t)c * m2 + s] = Pr[(size_t)sampled[s] * Mr + c];
+            PP[(size_t)c * m2 + ns + s] = Pr[(size_t)(n + sampled[s]) * Mr + c];
+        }
+    for (int d = 0; d < m2; ++d) Iden[(size_t)d * m2 + d] = 1.0;
+    lstsq_minnorm(m2, Mr, PP, Iden, m2, X);  // X = (P Phi_r)^+ (M_r x m2, column-major)
+    Ah.assign((size_t)Mr * m2, 0.0);
+    for (int d = 0; d < m2; ++d)
+        for (int r = 0; r < Mr; ++r) Ah[(size_t)r * m2 + d] = X[(size_t)d * Mr + r];
 }
 
 }  // namespace
@@ -1085,6 +1209,8 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     std::vector<float> xhf(Mp, 0.f), dxf(Mp, 0.f);
     std::vector<double> xh(M, 0.0), xprev(M), outh(nout);
     int nres = 0;
+    std::vector<double> tier2_traj;  // [n_params][steps + 1][M]
+    tier2_traj.reserve((size_t)n_params * (p->steps + 1) * M);
     // Tier II for every training parameter: its reference state, and the
     // cluster values recomputed from the stored memberships (as Sec. 5.2
     // reloads them), each run from xhat = 0
@@ -1127,6 +1253,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_CUDA(cudaMemcpyAsync(dx0c, x0cf.data(), sizeof(float) * x0cf.size(), cudaMemcpyHostToDevice, st));
     PTROM_CUDA(cudaMemcpyAsync(dgc, gcf.data(), sizeof(float) * NcA, cudaMemcpyHostToDevice, st));
     std::fill(xh.begin(), xh.end(), 0.0);
+    tier2_traj.insert(tier2_traj.end(), xh.begin(), xh.end());
     // f~ at xhat = 0 (R11)
     PTROM_CUDA(cudaMemsetAsync(dxh, 0, sizeof(float) * Mp, st));
     PTROM_CUDA(cudaMemsetAsync(ddx, 0, sizeof(float) * Mp, st));
@@ -1161,15 +1288,27 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
                 g2 += rhs[m] * rhs[m];
             }
             const double g = sqrt(g2);
+            // C = (I - dt/2 blockdiag D~) Phi has orthonormal Phi and a small
+            // perturbation, so its condition number is ~1 and the normal
+            // equations C^T C nu = -C^T r lose no accuracy against a QR of C;
+            // Cholesky solves them.  If C^T C is singular (a mode the dynamics
+            // leaves exactly unexcited), the minimum-norm solution
+            // nu = -(C^T C)^+ C^T r = -C^+ r is taken from its eigen-decomposition.
             if (!chol_solve(M, Gm, rhs)) {
-                // rank-deficient C (modes the trajectory does not excite): minimum-change
-                // step through a tiny ridge on the normal equations
-                double tr = 0.0;
-                for (int a = 0; a < M; ++a) tr += Gm[(size_t)a * M + a];
-                for (int a = 0; a < M; ++a) Gm[(size_t)a * M + a] += 1e-12 * (tr / M + 1e-300);
-                for (int a = 0; a < M; ++a) rhs[a] = -outh[(size_t)M * M + a];
-                if (!chol_solve(M, Gm, rhs))
-                    return set_error(PTROM_ENAN, "ptrom_build: singular Tier-II normal equations");
+                std::vector<double> w, V;
+                jacobi_eig(M, Gm, w, V);
+                const double cut = M * 2.220446049250313e-16 * std::max(w[0], 0.0);
+                std::vector<double> b(M);
+                for (int a = 0; a < M; ++a) b[a] = -outh[(size_t)M * M + a];
+                std::fill(rhs.begin(), rhs.end(), 0.0);
+                for (int j = 0; j < M; ++j) {
+                    if (!(w[j] > cut)) continue;
+                    double c = 0.0;
+                    for (int a = 0; a < M; ++a) c += V[(size_t)a * M + j] * b[a];
+                    c /= w[j];
+                    for (int a = 0; a < M; ++a) rhs[a] += c * V[(size_t)a * M + j];
+                }
+                if (!std::isfinite(rhs[0])) return set_error(PTROM_ENAN, "ptrom_build: non-finite Tier-II step");
             }
             for (int m = 0; m < M; ++m) xh[m] += rhs[m];
             if (first < 0.0) first = g;
@@ -1177,6 +1316,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
             if ((eps <= p->tol && k > 0) || first == 0.0) break;
         }
         PTROM_CUDA(cudaMemcpyAsync(dfp, df, sizeof(float) * nd, cudaMemcpyDeviceToDevice, st));
+        tier2_traj.insert(tier2_traj.end(), xh.begin(), xh.end());
     }
     }  // training parameters
     PTROM_CUDA(cudaStreamSynchronize(st));
@@ -1189,37 +1329,9 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     PTROM_TRY(pod_device(nd, nres, R, Mr_eff, st, Phir, sigr, true));
     std::vector<int> sampled = greedy_sample(Phir, n, Mr_eff, ns);
     if ((int)sampled.size() != ns) return set_error(PTROM_EINVAL, "ptrom_build: sampling found %zu bodies", sampled.size());
-    // A = [P Phi_r]^+ (Moore-Penrose, Eq. gappySolution).  P Phi_r is
-    // n_d x M_r.  With n_d >= M_r and full column rank, A solves
-    // min ||P Phi_r X - I||; with n_d < M_r (the gappy problem is then
-    // under-determined: the paper's mushroom cloud has n_d = 150 < M_r = 185)
-    // A is the minimum-norm right inverse, the transpose of (Phi_r^T P^T)^+.
     const int m2 = 2 * ns;
-    std::vector<double> Ah((size_t)Mr_eff * m2), X;
-    if (m2 >= Mr_eff) {
-        std::vector<double> PP((size_t)m2 * Mr_eff), Iden((size_t)m2 * m2, 0.0);
-        for (int s = 0; s < ns; ++s)
-            for (int c = 0; c < Mr_eff; ++c) {
-                PP[(size_t)c * m2 + s] = Phir[(size_t)sampled[s] * Mr_eff + c];
-                PP[(size_t)c * m2 + ns + s] = Phir[(size_t)(n + sampled[s]) * Mr_eff + c];
-            }
-        for (int d = 0; d < m2; ++d) Iden[(size_t)d * m2 + d] = 1.0;
-        if (!lstsq_qr(m2, Mr_eff, PP, Iden, m2, X))
-            return set_error(PTROM_EINVAL, "ptrom_build: P Phi_r is rank deficient");
-        for (int d = 0; d < m2; ++d)  // X is Mr x m2, column-major per column of I
-            for (int r = 0; r < Mr_eff; ++r) Ah[(size_t)r * m2 + d] = X[(size_t)d * Mr_eff + r];
-    } else {
-        std::vector<double> PT((size_t)Mr_eff * m2), Iden((size_t)Mr_eff * Mr_eff, 0.0);
-        for (int s = 0; s < ns; ++s)  // column d of (P Phi_r)^T = row d of P Phi_r
-            for (int c = 0; c < Mr_eff; ++c) {
-                PT[(size_t)s * Mr_eff + c] = Phir[(size_t)sampled[s] * Mr_eff + c];
-                PT[(size_t)(ns + s) * Mr_eff + c] = Phir[(size_t)(n + sampled[s]) * Mr_eff + c];
-            }
-        for (int r = 0; r < Mr_eff; ++r) Iden[(size_t)r * Mr_eff + r] = 1.0;
-        if (!lstsq_qr(Mr_eff, m2, PT, Iden, Mr_eff, X))
-            return set_error(PTROM_EINVAL, "ptrom_build: P Phi_r does not have full row rank");
-        Ah = X;  // column r of X is row r of A
-    }
+    std::vector<double> Ah;
+    gappy_operator(Phir, n, Mr_eff, sampled, Ah);
     // clusters of the sampled bodies, numbered by first appearance
     std::vector<int> off(ns + 1, 0), idx;
     std::vector<int> remap(NcA, -1), order;
@@ -1301,6 +1413,10 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
     m->A = Ah;
     m->cl_off = cl_off;
     m->cl_mem = cl_mem;
+    m->phi_r = Phir;
+    m->tier2_traj.swap(tier2_traj);
+    m->n_params = n_params;
+    m->steps = p->steps;
     const int e = model_store_basis(m, Phi.data(), x0h.data());
     if (e != PTROM_OK) {
         ptrom_free(m);
@@ -1401,5 +1517,60 @@ extern "C" int ptrom_model_query(const ptrom_model *m, int *n, int *M, int *M_r,
     if (sigma) std::copy(m->sigma.begin(), m->sigma.end(), sigma);
     if (sampled) std::copy(m->sampled.begin(), m->sampled.end(), sampled);
     if (A) std::copy(m->A.begin(), m->A.end(), A);
+    return PTROM_OK;
+}
+
+extern "C" int ptrom_greedy_sample(int n, int M_r, const double *phi_r, int n_s, int *sampled) {
+    if (n < 1 || M_r < 1 || n_s < 1 || n_s > n || !phi_r || !sampled)
+        return set_error(PTROM_EINVAL, "ptrom_greedy_sample: bad arguments (n=%d M_r=%d n_s=%d)", n, M_r, n_s);
+    std::vector<double> Pr(phi_r, phi_r + (size_t)2 * n * M_r);
+    const std::vector<int> s = greedy_sample(Pr, n, M_r, n_s);
+    if ((int)s.size() != n_s) return set_error(PTROM_EINVAL, "ptrom_greedy_sample: found %zu bodies", s.size());
+    std::copy(s.begin(), s.end(), sampled);
+    return PTROM_OK;
+}
+
+extern "C" int ptrom_gappy_operator(int n, int M_r, const double *phi_r, int n_s, const int *sampled, double *A) {
+    if (n < 1 || M_r < 1 || n_s < 1 || n_s > n || !phi_r || !sampled || !A)
+        return set_error(PTROM_EINVAL, "ptrom_gappy_operator: bad arguments (n=%d M_r=%d n_s=%d)", n, M_r, n_s);
+    for (int s = 0; s < n_s; ++s)
+        if (sampled[s] < 0 || sampled[s] >= n)
+            return set_error(PTROM_EINVAL, "ptrom_gappy_operator: sampled[%d]=%d out of range", s, sampled[s]);
+    std::vector<double> Pr(phi_r, phi_r + (size_t)2 * n * M_r), Ah;
+    gappy_operator(Pr, n, M_r, std::vector<int>(sampled, sampled + n_s), Ah);
+    std::copy(Ah.begin(), Ah.end(), A);
+    return PTROM_OK;
+}
+
+extern "C" int ptrom_model_query_training(const ptrom_model *m, int *M_r, int *n_params, int *steps, double *phi_r,
+                                          double *tier2_xhat) {
+    if (!m) return set_error(PTROM_EINVAL, "ptrom_model_query_training: NULL model");
+    if (!m->built || m->phi_r.empty())
+        return set_error(PTROM_EINVAL, "ptrom_model_query_training: no training data (the model was not made by "
+                                       "ptrom_build in this process)");
+    if (M_r) *M_r = m->d.Mr;
+    if (n_params) *n_params = m->n_params;
+    if (steps) *steps = m->steps;
+    if (phi_r) std::copy(m->phi_r.begin(), m->phi_r.end(), phi_r);
+    if (tier2_xhat) std::copy(m->tier2_traj.begin(), m->tier2_traj.end(), tier2_xhat);
+    return PTROM_OK;
+}
+
+extern "C" int ptrom_model_query_clusters(const ptrom_model *m, int *N_c, int *n_list, int *n_members, int *list_off,
+                                          int *list_idx, int *mem_off, int *mem, double *phi_c, double *x0_c,
+                                          double *gamma_c) {
+    if (!m) return set_error(PTROM_EINVAL, "ptrom_model_query_clusters: NULL model");
+    if (N_c) *N_c = m->d.Nc;
+    if (n_list) *n_list = (int)m->h_idx.size();
+    if (n_members) *n_members = (int)m->cl_mem.size();
+    if ((mem_off || mem) && !m->built)
+        return set_error(PTROM_EINVAL, "ptrom_model_query_clusters: memberships kept only by ptrom_build models");
+    if (list_off) std::copy(m->h_off.begin(), m->h_off.end(), list_off);
+    if (list_idx) std::copy(m->h_idx.begin(), m->h_idx.end(), list_idx);
+    if (mem_off) std::copy(m->cl_off.begin(), m->cl_off.end(), mem_off);
+    if (mem) std::copy(m->cl_mem.begin(), m->cl_mem.end(), mem);
+    if (phi_c) std::copy(m->h_phi_c.begin(), m->h_phi_c.end(), phi_c);
+    if (x0_c) std::copy(m->h_x0_c.begin(), m->h_x0_c.end(), x0_c);
+    if (gamma_c) std::copy(m->h_gamma_c.begin(), m->h_gamma_c.end(), gamma_c);
     return PTROM_OK;
 }

@@ -177,6 +177,7 @@ extern "C" int ptrom_load(const char *path, ptrom_model **out) {
         cl_mem = r.arr<int>(Lm);
         x0 = r.arr<double>(2 * (size_t)n);
         if (!r.ok) return set_error(PTROM_EINVAL, "ptrom_load: truncated or inconsistent built-model arrays");
+        if (cl_off[0] != 0) return set_error(PTROM_EINVAL, "ptrom_load: cluster offsets must start at 0");
         for (int c = 0; c < Nc; ++c)
             if (cl_off[c + 1] < cl_off[c]) return set_error(PTROM_EINVAL, "ptrom_load: cluster offsets not monotone");
         for (int v : cl_mem)

@@ -59,6 +59,9 @@ struct ptrom_model {
     std::vector<int> cl_off;      // [N_c + 1] cluster -> members (CSR)
     std::vector<int> cl_mem;
     std::vector<double> x0_full;  // [2n] the current parameter's x^0 (host copy of x0_dev)
+    std::vector<double> phi_r;    // [2n][M_r] row-major: the residual basis (Stage 3b)
+    std::vector<double> tier2_traj;  // [n_params][steps + 1][M]: Tier-II reduced trajectories
+    int n_params = 0, steps = 0;
     double *phi_dev = nullptr;    // [2n][M] FP64 (reconstruction)
     double *x0_dev = nullptr;     // [2n]
 };

@@ -139,6 +139,10 @@ def _load():
         "fom_step_batched": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, _vp, _vp,
                               ctypes.POINTER(FomStats), _vp], _i),
         "ptrom_set_pod_exact_max": ([_i], _i),
+        "ptrom_greedy_sample": ([_i, _i, _vp, _i, _vp], _i),
+        "ptrom_model_query_training": ([_vp] + [ctypes.POINTER(_i)] * 3 + [_vp, _vp], _i),
+        "ptrom_model_query_clusters": ([_vp] + [ctypes.POINTER(_i)] * 3 + [_vp] * 7, _i),
+        "ptrom_gappy_operator": ([_i, _i, _vp, _i, _vp, _vp], _i),
         "ptrom_save": ([_vp, ctypes.c_char_p], _i),
         "ptrom_load": ([ctypes.c_char_p, ctypes.POINTER(_vp)], _i),
         "fom_workspace_bytes": ([ctypes.POINTER(FomParams), _i], ctypes.c_size_t),
@@ -217,6 +221,28 @@ def timing_read() -> dict:
     cnt = (ctypes.c_longlong * k)()
     _check(lib.ptrom_timing_read(ms, cnt, k))
     return {name: (ms[i], int(cnt[i])) for i, name in enumerate(KERNEL_KINDS)}
+
+
+def greedy_sample(phi_r, n_s: int):
+    """Alg. 1 on the host: phi_r a (2n, M_r) float64 numpy array; returns the
+    n_s sampled body ids (numpy int32) in the order chosen."""
+    import numpy as np
+    P = np.ascontiguousarray(phi_r, dtype=np.float64)
+    n = P.shape[0] // 2
+    out = np.zeros(int(n_s), dtype=np.int32)
+    _check(lib.ptrom_greedy_sample(n, P.shape[1], P.ctypes.data, int(n_s), out.ctypes.data))
+    return out
+
+
+def gappy_operator(phi_r, sampled):
+    """A = [P Phi_r]^+ on the host: (M_r, 2 n_s) float64 numpy array."""
+    import numpy as np
+    P = np.ascontiguousarray(phi_r, dtype=np.float64)
+    s = np.ascontiguousarray(sampled, dtype=np.int32)
+    A = np.zeros((P.shape[1], 2 * s.size))
+    _check(lib.ptrom_gappy_operator(P.shape[0] // 2, P.shape[1], P.ctypes.data, s.size, s.ctypes.data,
+                                    A.ctypes.data))
+    return A
 
 
 def set_pod_exact_max(n: int) -> None:
@@ -388,6 +414,41 @@ class PtromModel:
                                      ctypes.c_void_p(phi.ctypes.data), ctypes.c_void_p(sig.ctypes.data),
                                      ctypes.c_void_p(smp.ctypes.data), ctypes.c_void_p(A.ctypes.data)))
         return {"phi": phi, "sigma": sig, "sampled": smp, "A": A}
+
+    def query_training(self):
+        """Training data of a model built in this process: phi_r (2n, M_r), the
+        residual basis Alg. 1 sampled on, and tier2 (n_params, steps + 1, M),
+        the Tier-II reduced trajectories."""
+        import numpy as np
+        Mr, npar, steps = _i(), _i(), _i()
+        _check(lib.ptrom_model_query_training(self.handle, ctypes.byref(Mr), ctypes.byref(npar), ctypes.byref(steps),
+                                              None, None))
+        phi_r = np.empty((2 * self.n, Mr.value))
+        t2 = np.empty((npar.value, steps.value + 1, self.M))
+        _check(lib.ptrom_model_query_training(self.handle, None, None, None, ctypes.c_void_p(phi_r.ctypes.data),
+                                              ctypes.c_void_p(t2.ctypes.data)))
+        return {"phi_r": phi_r, "tier2": t2}
+
+    def query_clusters(self):
+        """The online clusters: per sampled body the list of cluster ids, each
+        cluster's member bodies, and phi_c (2 N_c, M), x0_c (2 N_c), gamma_c (N_c)."""
+        import numpy as np
+        Nc, nl, nm = _i(), _i(), _i()
+        _check(lib.ptrom_model_query_clusters(self.handle, ctypes.byref(Nc), ctypes.byref(nl), ctypes.byref(nm),
+                                              *([None] * 7)))
+        off = np.empty(self.n_s + 1, dtype=np.int32)
+        idx = np.empty(max(nl.value, 1), dtype=np.int32)
+        moff = np.empty(Nc.value + 1, dtype=np.int32)
+        mem = np.empty(max(nm.value, 1), dtype=np.int32)
+        phi_c = np.empty((2 * Nc.value, self.M))
+        x0_c = np.empty(2 * Nc.value)
+        g_c = np.empty(Nc.value)
+        _check(lib.ptrom_model_query_clusters(self.handle, None, None, None,
+                                              *[ctypes.c_void_p(a.ctypes.data) for a in
+                                                (off, idx, moff, mem, phi_c, x0_c, g_c)]))
+        lists = [idx[off[s]:off[s + 1]].tolist() for s in range(self.n_s)]
+        members = [mem[moff[c]:moff[c + 1]].tolist() for c in range(Nc.value)]
+        return {"lists": lists, "members": members, "phi_c": phi_c, "x0_c": x0_c, "gamma_c": g_c}
 
     def set_param_full(self, x0, Gamma, stream=None):
         """Reload the clusters for a new parameter (device x0 [2n], Gamma [n])."""
