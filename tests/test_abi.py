@@ -126,3 +126,38 @@ def test_binding_structs_match_the_header_layout(lib, tmp_path):
         assert int(c[cname]) == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert int(c[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
+
+
+def _fnv1a(data: bytes) -> int:
+    h = 1469598103934665603
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _model_file(cl_off):
+    """A built-model file in the documented layout (ptrom_io.cu), correctly
+    hashed: n_s = M = M_r = N_c = 1, n = 2, with the given cluster offsets."""
+    import struct
+    f64 = lambda *v: struct.pack("<Q", len(v)) + struct.pack(f"<{len(v)}d", *v)
+    i32 = lambda *v: struct.pack("<Q", len(v)) + struct.pack(f"<{len(v)}i", *v)
+    body = b"PTROMMDL" + struct.pack("<II", 0x01020304, 2)
+    body += struct.pack("<8i", 1, 1, 1, 1, 10, 0, 1, 2)            # n_s M M_r N_c max_gn qr_prec built n
+    body += struct.pack("<5d", 0.01, 0.05, 1e-4, 0.0, 0.0)
+    body += f64(0.1, 0.2) + f64(0.0, 0.0) + f64(0.3, 0.4) + f64(1.0, 1.0) + f64(1.0) + f64(0.5, 0.5)
+    body += i32(0, 1) + i32(0) + f64()                                # off, idx, u_s (none)
+    body += f64(1.0, 0.0, 0.0, 0.0) + f64(1.0) + i32(0) + i32(*cl_off) + i32() + f64(0.0, 1.0, 0.0, 0.0)
+    return body + struct.pack("<Q", _fnv1a(body))
+
+
+def test_model_file_with_cluster_offsets_not_from_zero_is_rejected(lib, tmp_path):
+    """A crafted, correctly hashed file whose cluster-member offsets start at
+    -1 would make a later reload index before the member array; ptrom_load
+    rejects it on the host, before any CUDA call."""
+    L = lib.lib
+    h = ctypes.c_void_p(0)
+    bad = tmp_path / "bad_cl_off.bin"
+    bad.write_bytes(_model_file([-1, 0]))
+    assert L.ptrom_load(str(bad).encode(), ctypes.byref(h)) == -1
+    assert "start at 0" in lib.last_error()
+    assert not h.value
