@@ -299,6 +299,7 @@ def run_ours(args):
                    "pairs_per_s": n * n * c / (t * 1e-3),
                    "tflops": FLOPS_PER_PAIR[k] * n * n * c / (t * 1e-3) / 1e12}
                for k, (t, c) in ktimes.items() if c and k in FLOPS_PER_PAIR}
+    kernels["jphi"] = _jphi_leg(ptrom, dev, flush)
     other = _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush)
 
     # end to end: host buffers, H2D of the step's inputs and D2H of its result
@@ -600,6 +601,36 @@ def batch_leg(ptrom, dev):
         "batched_fom_step_pairs_per_s": evals_b / tb_step,
         "fom_mode": "block-diagonal inexact Newton (the paper's), FP32C pair sums",
     }
+
+
+def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5):
+    """J Phi (the LSPG basis product) on the two-cluster workload at N = 65536
+    with M = 60 random basis columns: library-side events on its launches (the
+    source-split sum included), L2 flushed before each."""
+    import numpy as np
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    x0, G = W.two_cluster(n, seed=0)
+    x = torch.tensor(x0, device=dev)
+    Gt = torch.tensor(G, device=dev)
+    phi = torch.tensor(np.random.default_rng(5).standard_normal((2 * n, M)) / np.sqrt(2 * n), device=dev)
+    for _ in range(2):
+        ptrom.bs_jphi(x, Gt, WORKLOAD["delta"], phi)
+    torch.cuda.synchronize(dev)
+    ptrom.timing_read()
+    ptrom.timing_enable(True, kinds=["jphi"])
+    for _ in range(reps):
+        flush.zero_()
+        ptrom.bs_jphi(x, Gt, WORKLOAD["delta"], phi)
+    torch.cuda.synchronize(dev)
+    ptrom.timing_enable(False)
+    t, c = ptrom.timing_read()["jphi"]
+    flops = 20 + 8 * M  # per pair: the 2x2 block, then 4 multiply-adds per column
+    pps = n * n * c / (t * 1e-3)
+    return {"n": n, "M": M, "launches": c, "avg_us": 1e3 * t / c, "pairs_per_s": pps,
+            "flops_per_pair": flops, "tflops": flops * pps / 1e12, "units": "SIMT FP32 pair blocks, FP32 compensated"}
 
 
 def _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush, steps=10):

@@ -2,14 +2,19 @@
 //     (J Phi)_i = sum_{j != i} gamma_j A(x_i - x_j) (Phi_i - Phi_j)
 // (the J Phi of the LSPG Gauss-Newton problem, Sec. 3.2, with J = d f/d x).
 //
-// One thread per target, 16 basis columns per grid.y slice: the 2x2 pair block
-// gamma_j A is generated once per pair on the FP32 pipes and applied to the 16
+// One thread per target, 12 basis columns per grid.y slice: the 2x2 pair block
+// gamma_j A is generated once per pair on the FP32 pipes and applied to the 12
 // columns' row differences with packed FFMA2 (two columns per instruction).
 // Sources are packed once (positions relative to a common origin, gamma, and
-// their 16 negated Phi rows per slice) and staged 32 at a time in shared
-// memory.  gridDim.z splits the sources; partial sums meet in the FP64 output
-// through atomic adds (the output is zeroed first).  An FP64 variant (one
-// thread per target and column) serves checking.
+// their 12 negated Phi rows per slice) and staged 32 at a time in shared
+// memory.  Accumulation: the 32 pair terms of a staged round are summed in
+// plain FP32, then folded into a TwoSum-compensated (hi, lo) pair per output.
+// gridDim.z splits the sources; each split writes its FP64 partial to
+// scratch and a second kernel adds the splits in split order, so results are
+// the same run to run.  An FP64 variant (one thread per target and column)
+// serves checking.
+#include <algorithm>
+
 #include "common.cuh"
 #include "scratch.h"
 #include "internal.h"
@@ -18,7 +23,11 @@ namespace ptrom {
 namespace {
 
 constexpr int kJT = 128;  // targets per CTA
-constexpr int kMC = 16;   // basis columns per slice
+// basis columns per slice: 12 (measured on GB300 against 8 and 16 with the
+// compensated sums: 16 needs 190 registers per thread, 8 repeats the pair
+// block's generation too often; at N = 65536, M = 60: 6.2e10, 6.7e10 and
+// 6.0e10 pairs/s for 8, 12 and 16)
+constexpr int kMC = 12;
 constexpr int kJS = 32;   // sources per shared-memory round
 
 struct __align__(16) JRec {
@@ -57,14 +66,15 @@ __global__ void k_jphi_pack(int n, const double *x, const double *G, const doubl
 template <bool MASK>
 __global__ void __launch_bounds__(kJT)
 k_jphi(int n, const double *x, const double *phi, int M, float delta, const JRec *__restrict__ packed, int ns_pad,
-       int nchunks, double *out) {
+       int nchunks, double *out, double *part) {
     __shared__ JRec src[kJS];
     const int i = blockIdx.x * kJT + threadIdx.x;
     const int slice = blockIdx.y;
     const bool active = i < n;
     const double ox = x[0], oy = x[n];
     const float tx = active ? (float)(x[i] - ox) : 0.f, ty = active ? (float)(x[n + i] - oy) : 0.f;
-    float2 pc[kMC / 2], pp[kMC / 2], ac[kMC / 2], ap[kMC / 2];
+    float2 pc[kMC / 2], pp[kMC / 2];
+    CSum2 ac[kMC / 2], ap[kMC / 2];  // compensated sums over rounds
 #pragma unroll
     for (int k = 0; k < kMC / 2; ++k) {
         float c[2], p[2];
@@ -76,8 +86,8 @@ k_jphi(int n, const double *x, const double *phi, int M, float delta, const JRec
         }
         pc[k] = make_float2(c[0], c[1]);
         pp[k] = make_float2(p[0], p[1]);
-        ac[k] = make_float2(0.f, 0.f);
-        ap[k] = make_float2(0.f, 0.f);
+        ac[k].zero();
+        ap[k].zero();
     }
     const JRec *base = packed + (size_t)slice * ns_pad;
     const int c_begin = (int)(((long long)blockIdx.z * nchunks) / gridDim.z);
@@ -87,6 +97,12 @@ k_jphi(int n, const double *x, const double *phi, int M, float delta, const JRec
         for (int e = threadIdx.x; e < kJS * (int)(sizeof(JRec) / 16); e += kJT)
             reinterpret_cast<float4 *>(src)[e] = __ldg(reinterpret_cast<const float4 *>(base + (size_t)c * kJS) + e);
         __syncthreads();
+        float2 tc[kMC / 2], tq[kMC / 2];  // this round's plain FP32 sums
+#pragma unroll
+        for (int k = 0; k < kMC / 2; ++k) {
+            tc[k] = make_float2(0.f, 0.f);
+            tq[k] = make_float2(0.f, 0.f);
+        }
 #pragma unroll 2
         for (int s = 0; s < kJS; ++s) {
             const JRec &r = src[s];
@@ -104,30 +120,39 @@ k_jphi(int n, const double *x, const double *phi, int M, float delta, const JRec
             for (int k = 0; k < kMC / 2; ++k) {
                 const float2 dc = __fadd2_rn(pc[k], r.nc[k]);
                 const float2 dp = __fadd2_rn(pp[k], r.np[k]);
-                ac[k] = __ffma2_rn(A00, dc, ac[k]);
-                ac[k] = __ffma2_rn(A01, dp, ac[k]);
-                ap[k] = __ffma2_rn(A10, dc, ap[k]);
-                ap[k] = __ffma2_rn(N00, dp, ap[k]);
+                tc[k] = __ffma2_rn(A00, dc, tc[k]);
+                tc[k] = __ffma2_rn(A01, dp, tc[k]);
+                tq[k] = __ffma2_rn(A10, dc, tq[k]);
+                tq[k] = __ffma2_rn(N00, dp, tq[k]);
             }
+        }
+#pragma unroll
+        for (int k = 0; k < kMC / 2; ++k) {
+            ac[k].add(tc[k]);
+            ap[k].add(tq[k]);
         }
     }
     if (!active) return;
-    const bool split = gridDim.z > 1;
+    // one split: the output itself; several: this split's slab of the partials
+    double *dst = gridDim.z > 1 ? part + (size_t)blockIdx.z * 2 * n * M : out;
 #pragma unroll
     for (int k = 0; k < kMC / 2; ++k) {
-        const float vc[2] = {ac[k].x, ac[k].y}, vp[2] = {ap[k].x, ap[k].y};
+        const double vc[2] = {ac[k].x(), ac[k].y()}, vp[2] = {ap[k].x(), ap[k].y()};
         for (int h = 0; h < 2; ++h) {
             const int m = slice * kMC + 2 * k + h;
             if (m >= M) continue;
-            double *oc = out + (size_t)m * 2 * n + i, *op = out + (size_t)m * 2 * n + n + i;
-            if (split) {
-                atomicAdd(oc, (double)vc[h]);
-                atomicAdd(op, (double)vp[h]);
-            } else {
-                *oc = vc[h];
-                *op = vp[h];
-            }
+            dst[(size_t)m * 2 * n + i] = vc[h];
+            dst[(size_t)m * 2 * n + n + i] = vp[h];
         }
+    }
+}
+
+// out = sum over the S splits' partials, in split order.
+__global__ void k_jphi_sum(size_t len, int S, const double *__restrict__ part, double *__restrict__ out) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int s = 0; s < S; ++s) v += part[(size_t)s * len + e];
+        out[e] = v;
     }
 }
 
@@ -179,21 +204,29 @@ int jphi(int n, const double *x, const double *G, double delta, const double *ph
         while ((long long)tblocks * nslices * S * 2 <= want && (S * 2) * 4 <= nchunks) S *= 2;
     }
     JRec *packed = nullptr;
+    double *part = nullptr;
+    const size_t len = 2 * (size_t)n * M;
     ScratchScope sc(st);
     PTROM_TRY(sc.alloc(&packed, sizeof(JRec) * (size_t)nslices * ns_pad));
+    if (S > 1) PTROM_TRY(sc.alloc(&part, sizeof(double) * len * S));
     int pgrid = (nslices * ns_pad + 255) / 256;
     if (pgrid > 8 * device_sm_count()) pgrid = 8 * device_sm_count();
     k_jphi_pack<<<pgrid, 256, 0, st>>>(n, x, G, phi, M, nslices, ns_pad, packed);
     count_launch();
-    if (S > 1) PTROM_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)n * M, st));
     dim3 grid(tblocks, nslices, S);
     const int slot = timing_begin(PTROM_K_JPHI, st);
     if (delta == 0.0)
-        k_jphi<true><<<grid, kJT, 0, st>>>(n, x, phi, M, (float)delta, packed, ns_pad, nchunks, out);
+        k_jphi<true><<<grid, kJT, 0, st>>>(n, x, phi, M, (float)delta, packed, ns_pad, nchunks, out, part);
     else
-        k_jphi<false><<<grid, kJT, 0, st>>>(n, x, phi, M, (float)delta, packed, ns_pad, nchunks, out);
+        k_jphi<false><<<grid, kJT, 0, st>>>(n, x, phi, M, (float)delta, packed, ns_pad, nchunks, out, part);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && S > 1) {
+        int rgrid = (int)std::min<size_t>((len + 255) / 256, (size_t)8 * device_sm_count());
+        k_jphi_sum<<<rgrid, 256, 0, st>>>(len, S, part, out);
+        e = cudaGetLastError();
+        count_launch();
+    }
     timing_end(slot, st);
-    const cudaError_t e = cudaGetLastError();
     PTROM_TRY(sc.release());
     if (e != cudaSuccess) return check_cuda(e, "k_jphi launch");
     count_launch();

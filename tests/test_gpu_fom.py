@@ -127,6 +127,43 @@ def test_full_size_step_residual_sampled(P):
         xp = xn
 
 
+def test_mixed_precision_scale_up_500_steps(P):
+    """The mixed-precision scale-up workload in full: N = 16384 two clusters,
+    delta = 0.02, dt = 0.005, 500 implicit steps by JFNK with FP32C pair
+    sums.  Every 50 steps the library's velocity at its own state is checked
+    against the FP64 oracle on 256 sampled bodies (rel-L2 <= 1e-5); the
+    circulation is constant, the linear impulse (an exact invariant of the
+    trapezoid rule, kept to the Newton tolerance) drifts by at most 1e-7 of
+    sum |Gamma_i| |x_i|, and the angular impulse, which the trapezoid rule
+    does not conserve exactly, is reported."""
+    n, delta, dt, steps = 16384, 0.02, 0.005, 500
+    x0, G = W.two_cluster(n, seed=0)
+    params = P.fom_params(dt, delta, "jfnk", prec="fp32c")
+    x, Gt = _dev(x0), _dev(G)
+    f = P.bs_velocity(x, Gt, delta)
+    work = P.fom_workspace(params, n)
+    rows = np.random.default_rng(41).choice(n, 256, replace=False)
+    idx = np.r_[rows, n + rows]
+    scale = float(np.sum(np.abs(G) * np.hypot(x0[:n], x0[n:])))
+    P0, I0 = qoi.linear_impulse(x0, G), qoi.angular_impulse(x0, G)
+    report = []
+    for k in range(1, steps + 1):
+        P.fom_step(params, Gt, x, f, work=work)
+        if k % 50 == 0:
+            xn = x.cpu().numpy()
+            fo = direct.velocity(xn, G, delta, targets=xn[idx])
+            rel_f = np.linalg.norm(f.cpu().numpy()[idx] - fo) / np.linalg.norm(fo)
+            dP = float(np.abs(qoi.linear_impulse(xn, G) - P0).max()) / scale
+            dI = abs(qoi.angular_impulse(xn, G) - I0) / abs(I0)
+            report.append((k, rel_f, dP, dI))
+            assert rel_f <= 1e-5, (k, rel_f)
+            assert dP <= 1e-7, (k, dP)
+    assert float(Gt.sum()) == pytest.approx(float(G.sum()), abs=0)
+    for k, rel_f, dP, dI in report:
+        print(f"step {k:3d}: velocity rel-L2 {rel_f:.2e}, linear impulse drift {dP:.1e}, "
+              f"angular impulse drift {dI:.1e}")
+
+
 @pytest.mark.parametrize("restart", [1, 2, 3])
 def test_jfnk_short_restart_cycles_fp64(P, restart):
     """GMRES(m) with m = 1..3 and a tight tolerance runs several cycles per

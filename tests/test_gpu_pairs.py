@@ -200,3 +200,23 @@ def test_jphi_full_size_sampled_rows(P):
     idx = np.r_[rows, n + rows]
     ref = np.stack([direct.jvp(x, G, 0.02, phi[:, m], rows=rows) for m in range(M)], axis=1)
     assert _rel(out[idx], ref) <= 1e-5
+
+
+@pytest.mark.parametrize("split", [1, 3, 7])
+def test_jphi_source_splits_are_deterministic(P, split):
+    """J Phi with its sources split over 1, 3 or 7 CTAs per target block: the
+    splits' partials are added in a fixed order, so two launches agree bit
+    for bit, and every split agrees with the oracle (M = 25 leaves a ragged
+    last 12-column slice)."""
+    n, M = 2050, 25
+    x, G = W.two_cluster(n, seed=65)
+    phi = W.random_vectors(x.size, M, seed=66).T
+    ref = direct.jphi(x, G, 0.02, phi)
+    P.set_source_split(split)
+    try:
+        a = P.bs_jphi(_dev(x), _dev(G), 0.02, _dev(phi))
+        b = P.bs_jphi(_dev(x), _dev(G), 0.02, _dev(phi))
+    finally:
+        P.set_source_split(0)
+    assert torch.equal(a, b)
+    assert _rel(a.cpu().numpy(), ref) <= 1e-5
