@@ -48,6 +48,7 @@ WORKLOAD = {
     "newton_tol": 1e-8,
     "gmres": "restart 30, rtol 1e-4, block-diagonal right preconditioner",
     "l2": "flushed (256 MB memset) before every timed step",
+    "source_split": "autotuned per all-pairs kernel before the warm-up steps (ptrom_tune_pairs)",
 }
 # Algorithmic work per pair (an FMA counts 2 flops, the reciprocal 1), the
 # per-unit figures the roofline is quoted on: velocity = 2 differences +
@@ -242,6 +243,7 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
+    ptrom.tune_pairs(n, delta)  # cache the fastest source split of each all-pairs kernel at this size
     for _ in range(args.warmup):
         ptrom.fom_step(params, Gt, x, f, work=work)
     torch.cuda.synchronize(dev)
@@ -540,6 +542,216 @@ def parametric_leg(ptrom, dev, which, qr_prec="fp64"):
             "queries": [[round(a, 2), round(b, 2), m, h, sp] for a, b, m, h, sp in rows]}
 
 
+def _fom_run(ptrom, fp, x0, G, steps, dev, every, keep_all=False):
+    """GPU FOM trajectory of `steps` steps: states every `every` steps (and,
+    with keep_all, every state as the training snapshots), device ms per step."""
+    import torch
+    n = G.size
+    x = torch.tensor(x0, device=dev)
+    Gd = torch.tensor(G, device=dev)
+    f = ptrom.bs_velocity(x, Gd, fp.delta)
+    work = ptrom.fom_workspace(fp, n, dev)
+    allx = torch.empty(steps, 2 * n, dtype=torch.float64, device=dev) if keep_all else None
+    ref = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for k in range(1, steps + 1):
+        ptrom.fom_step(fp, Gd, x, f, work=work)
+        if keep_all:
+            allx[k - 1] = x
+        if k % every == 0:
+            ref[k] = x.clone()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return allx, ref, e0.elapsed_time(e1) / steps
+
+
+def c3_leg(ptrom, dev, n=65536, steps=1000, ks=(20, 40, 60), mults=(2, 4), theta=0.5, every=25):
+    """The parametric PTROM configuration: two-cluster bodies with common random
+    numbers, separation in [0.8, 1.2] and circulation ratio in [0.5, 2.0];
+    trained (offline, untimed) on the GPU FOM at 8 Latin-hypercube parameters
+    (seed 1), queried at 4 held-out ones (seed 2); POD rank k, M_r = 2k,
+    n_s = mult * k sampled bodies, Barnes-Hut theta, FP64 least squares.
+    Per configuration and held-out parameter: time-averaged MAE_D and AE_H of
+    the PTROM against the GPU FOM, of the best point of the trial manifold
+    (the basis alone), and of Tier II on the first training parameter (the
+    clustered LSPG over all bodies); a speed-up only where both PTROM QoIs
+    stay within 0.1 %."""
+    import numpy as np
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    delta, dt = WORKLOAD["delta"], WORKLOAD["dt"]
+    fp = ptrom.fom_params(dt, delta, "jfnk", tol=WORKLOAD["newton_tol"], prec="fp32c")
+    train, held = W.param_lhs(8, seed=1), W.param_lhs(4, seed=2)
+    t0 = time.perf_counter()
+    snaps, x0s, gs, train_ref = [], [], [], None
+    for q, (sep, ratio) in enumerate(train):
+        x0, G = W.two_cluster(n, seed=0, sep=sep, ratio=ratio)
+        allx, ref, _ = _fom_run(ptrom, fp, x0, G, steps, dev, every, keep_all=True)
+        snaps.append(allx)
+        x0s.append(x0)
+        gs.append(G)
+        if q == 0:
+            train_ref = ref
+    S = torch.cat(snaps)
+    del snaps
+    X0 = torch.tensor(np.stack(x0s), device=dev)
+    GS = torch.tensor(np.stack(gs), device=dev)
+    held_runs = []
+    for sep, ratio in held:
+        x0, G = W.two_cluster(n, seed=0, sep=sep, ratio=ratio)
+        _, ref, fom_ms = _fom_run(ptrom, fp, x0, G, steps, dev, every)
+        Gd = torch.tensor(G, device=dev)
+        held_runs.append({"sep": float(sep), "ratio": float(ratio), "x0": x0, "G": G, "Gd": Gd, "ref": ref,
+                          "fom_ms": fom_ms, "H": {k: _hamiltonian_gpu(v, Gd, n) for k, v in ref.items()}})
+    fom_s = time.perf_counter() - t0
+    out = {"workload": (f"two clusters, N={n}, delta={delta}, dt={dt}, {steps} steps; 8 LHS training parameters "
+                        f"(seed 1), 4 held-out (seed 2); M_r = 2k; Barnes-Hut theta={theta}; FP64 least squares; "
+                        f"QoIs time-averaged over every {every}th step against the GPU FOM"),
+           "fom_seconds": fom_s, "configs": []}
+    l_of = lambda x0: float(np.hypot(x0[n - 1] - x0[0], x0[2 * n - 1] - x0[n]))
+
+    def qois(recs, run):
+        """time-averaged MAE_D and AE_H of the states recs[k] against run's FOM"""
+        l = l_of(run["x0"])
+        mae, aeh = [], []
+        for k, xr in run["ref"].items():
+            xp = recs[k]
+            d = torch.sqrt((xp[:n] - xr[:n]) ** 2 + (xp[n:] - xr[n:]) ** 2)
+            mae.append(float(d.sum()) / (l * n))
+            aeh.append(abs(_hamiltonian_gpu(xp, run["Gd"], n) - run["H"][k]) / abs(run["H"][k]))
+        return float(np.mean(mae)), float(np.mean(aeh))
+
+    for k in ks:
+        for mult in mults:
+            cfg = {"k": k, "M_r": 2 * k, "n_s": mult * k}
+            t0 = time.perf_counter()
+            try:
+                model, info = ptrom.ptrom_build(X0, GS, k, 2 * k, mult * k, steps, fp, criterion="bh",
+                                                theta=theta, tol=1e-4, qr_prec="fp64", snapshots=S)
+            except ptrom.PtromError as e:
+                cfg["error"] = str(e)
+                out["configs"].append(cfg)
+                continue
+            cfg.update(build_s=time.perf_counter() - t0, N_c=info["N_c"],
+                       mean_clusters_per_sampled_body=info["mean_list"])
+            q = model.query()
+            Phi = torch.tensor(q["phi"], device=dev)
+            t2 = torch.tensor(model.query_training()["tier2"][0], device=dev)
+            x0t = torch.tensor(x0s[0], device=dev)
+            run0 = {"x0": x0s[0], "Gd": GS[0], "ref": train_ref,
+                    "H": {kk: _hamiltonian_gpu(v, GS[0], n) for kk, v in train_ref.items()}}
+            cfg["tier2_train0"] = qois({kk: x0t + Phi @ t2[kk] for kk in train_ref}, run0)
+            rows = []
+            for run in held_runs:
+                x0d = torch.tensor(run["x0"], device=dev)
+                best = {kk: x0d + Phi @ (Phi.T @ (xr - x0d)) for kk, xr in run["ref"].items()}
+                model.set_param_full(x0d, run["Gd"])
+                st = model.new_state(dev)
+                hist = torch.zeros(steps, k, dtype=torch.float64, device=dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record()
+                stats = ptrom.ptrom_step([model], [st], steps, hist=[hist])
+                e1.record()
+                torch.cuda.synchronize(dev)
+                rom_us = 1e3 * e0.elapsed_time(e1) / steps
+                rec = {kk: model.reconstruct(hist[kk - 1]) for kk in run["ref"]}
+                m_p, h_p = qois(rec, run)
+                m_b, h_b = qois(best, run)
+                within = m_p <= QOI_BOUND and h_p <= QOI_BOUND
+                row = {"sep": run["sep"], "ratio": run["ratio"], "mae_d": m_p, "ae_h": h_p,
+                       "best_mae_d": m_b, "best_ae_h": h_b, "ptrom_us_per_step": rom_us,
+                       "fom_ms_per_step": run["fom_ms"], "gn_iters_per_step": stats["gn_iters"] / steps,
+                       "noconv_steps": stats["noconv"], "within_qoi_bound": within}
+                row["speedup_vs_gpu_fom_step" if within else "step_time_ratio_vs_gpu_fom_outside_qoi_bound"] = \
+                    1e3 * run["fom_ms"] / rom_us
+                rows.append(row)
+            cfg["held_out"] = rows
+            out["configs"].append(cfg)
+            del model, Phi
+    return out
+
+
+# Sec. 6.4's PTROM hyper-parameters: per neighbourhood width (Tables 2-4) and
+# bases case (tolerance 1e-1 .. 1e-4), M and p_c for N = 100 .. 5000, and the
+# paper's resulting N_c.  M_r = 2M and n_s = M_r throughout.
+SV_NS = (100, 500, 1000, 2000, 3000, 4000, 5000)
+SV_TOL = (1e-1, 1e-2, 1e-3, 1e-4)
+SV_M = {"narrow": ((13, 21, 21, 21, 23, 23, 23), (14, 22, 22, 22, 23, 23, 24), (14, 23, 23, 23, 25, 25, 26),
+                   (16, 24, 24, 26, 26, 26, 26)),
+        "moderate": ((13, 21, 21, 21, 23, 23, 23), (14, 22, 22, 22, 23, 23, 24), (14, 23, 23, 23, 25, 25, 26),
+                     (18, 24, 24, 26, 26, 26, 26)),
+        "wide": ((13, 21, 21, 21, 23, 23, 23), (14, 22, 22, 22, 23, 23, 24), (14, 23, 23, 23, 25, 25, 26),
+                 (18, 24, 24, 26, 26, 32, 33))}
+SV_PC = {"narrow": ((0,) * 7, (0,) * 7, (0,) * 7, (0, 0, 0, 0, 0.5, 0.5, 0.5)),
+         "moderate": ((1,) * 7,) * 4, "wide": ((2,) * 7,) * 4}
+SV_NC = {"narrow": ((68, 113, 121, 122, 134, 131, 142), (69, 114, 129, 127, 142, 130, 140),
+                    (70, 120, 132, 134, 136, 143, 156), (80, 128, 130, 134, 151, 159, 144)),
+         "moderate": ((73, 122, 139, 123, 135, 137, 149), (79, 130, 142, 149, 137, 150, 144),
+                      (79, 127, 133, 132, 146, 153, 149), (84, 131, 144, 144, 147, 159, 143)),
+         "wide": ((79, 133, 135, 143, 161, 183, 154), (80, 130, 154, 153, 164, 155, 159),
+                  (80, 136, 146, 165, 178, 173, 173), (113, 150, 143, 167, 194, 216, 213))}
+
+
+def single_vortex_leg(ptrom, dev, ns=SV_NS, widths=("narrow", "moderate", "wide"), cases=(0, 1, 2, 3)):
+    """Sec. 6.4's reproductive single-vortex experiment (Table 1 conditions,
+    delta = 0) for the PTROM settings of Tables 2-4: per N, one FP64 GPU FOM
+    trajectory (JFNK) gives the snapshots; per (width, bases case) a PTROM is
+    trained on them and run over the same steps.  Reported: N_c beside the
+    paper's, time-averaged MAE_D and AE_H against the FOM (the paper reports all
+    below 0.1 %), Gauss-Newton iterations and step times."""
+    import numpy as np
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    out = []
+    for n in ns:
+        col = SV_NS.index(n)
+        x0, G, dt, steps = W.single_vortex(n)
+        fp = ptrom.fom_params(dt, 0.0, "jfnk", tol=1e-12, prec="fp64", gmres_rtol=1e-10, gmres_max_iter=400)
+        allx, _, fom_ms = _fom_run(ptrom, fp, x0, G, steps, dev, steps, keep_all=True)
+        Gd = torch.tensor(G, device=dev)
+        xd = torch.tensor(x0, device=dev)
+        l = float(np.hypot(x0[n - 1] - x0[0], x0[2 * n - 1] - x0[n]))
+        chk = list(range(99, steps, 100))
+        H = {k: _hamiltonian_gpu(allx[k], Gd, n) for k in chk}
+        for width in widths:
+            for case in cases:
+                M, pc = SV_M[width][case][col], SV_PC[width][case][col]
+                row = {"n": n, "width": width, "bases_case": case + 1, "tol": SV_TOL[case], "M": M, "p_c": pc,
+                       "paper_N_c": SV_NC[width][case][col]}
+                try:
+                    model, info = ptrom.ptrom_build(xd[None], Gd[None], M, 2 * M, 2 * M, steps, fp, criterion="nb",
+                                                    p_c=pc, tol=SV_TOL[case], qr_prec="fp64", snapshots=allx)
+                except ptrom.PtromError as e:
+                    row["error"] = str(e)
+                    out.append(row)
+                    continue
+                st = model.new_state(dev)
+                hist = torch.zeros(steps, M, dtype=torch.float64, device=dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                stats = ptrom.ptrom_step([model], [st], steps, hist=[hist])
+                e1.record()
+                torch.cuda.synchronize(dev)
+                rec = torch.stack([model.reconstruct(hist[k]) for k in range(steps)])
+                mae = float((torch.sqrt((rec[:, :n] - allx[:, :n]) ** 2 + (rec[:, n:] - allx[:, n:]) ** 2)
+                             .mean(dim=1) / l).mean())
+                aeh = float(np.mean([abs(_hamiltonian_gpu(rec[k], Gd, n) - H[k]) / abs(H[k]) for k in chk]))
+                row.update(N_c=info["N_c"], mae_d=mae, ae_h=aeh, gn_iters_per_step=stats["gn_iters"] / steps,
+                           noconv_steps=stats["noconv"], ptrom_us_per_step=1e3 * e0.elapsed_time(e1) / steps,
+                           fom_ms_per_step=fom_ms)
+                out.append(row)
+                del model
+        del allx
+    return out
+
+
 def batch_leg(ptrom, dev):
     """Batched FOM over 64 instances of uneven N (log-uniform in [4096,
     131072], separation and circulation ratio uniform in their ranges, seed 3):
@@ -764,6 +976,13 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--vortex-pair", action="store_true",
                     help="also run the paper's vortex-pair parametric experiment (about 3 minutes)")
+    ap.add_argument("--single-vortex", action="store_true",
+                    help="run only the single-vortex leg (Table 1 conditions, Tables 2-4 settings) and print it")
+    ap.add_argument("--sv-n", type=str, default=",".join(map(str, SV_NS)), help="bodies of the --single-vortex leg")
+    ap.add_argument("--c3", action="store_true",
+                    help="run only the parametric PTROM leg (8 training, 4 held-out parameters) and print it")
+    ap.add_argument("--c3-n", type=int, default=65536, help="bodies of the --c3 leg")
+    ap.add_argument("--c3-steps", type=int, default=1000, help="time steps of the --c3 leg")
     ap.add_argument("--mushroom", action="store_true",
                     help="also run the paper's mushroom-cloud parametric experiment (about 5 minutes)")
     ap.add_argument("--qr-prec", choices=["fp64", "fp32c"], default="fp64",
@@ -774,6 +993,18 @@ def main():
     args = ap.parse_args()
     if args.kernel_only:
         kernel_only(args)
+        return
+    if args.single_vortex:
+        import torch
+        from paper_2103_01983_gb300 import ptrom
+        ns = tuple(int(v) for v in args.sv_n.split(","))
+        print(json.dumps({"single_vortex": single_vortex_leg(ptrom, torch.device("cuda", 0), ns=ns)}), flush=True)
+        return
+    if args.c3:
+        import torch
+        from paper_2103_01983_gb300 import ptrom
+        print(json.dumps({"c3": c3_leg(ptrom, torch.device("cuda", 0), n=args.c3_n, steps=args.c3_steps)}),
+              flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -76,6 +76,25 @@ int ptrom_version(void);
 int ptrom_set_source_split(int S);
 int ptrom_set_split_mode(int mode);
 
+/* Autotuning of the all-pairs source split S (with the global combine; a
+ * forced S or the cluster combine bypasses it).
+ * ptrom_tune_pairs(n, prec, delta, stream): times every S in 1..16 that
+ *   leaves each warp at least 32 sources, for each all-pairs kernel the
+ *   FOM step uses at n targets x n sources (velocity, velocity with self
+ *   blocks, J v, J^T w with and without (df/dGamma)^T w) on synthetic
+ *   bodies, and caches the fastest per (kernel, device, n, n); later launches
+ *   of those shapes take it.  Synchronises the stream; allocates scratch from
+ *   the library pool.  PTROM_EINVAL as bs_velocity.
+ * ptrom_set_autotune(on): on = 1 tunes, the first time, any launch shape
+ *   without a cached split (on the caller's data; not while the stream is
+ *   being captured, and not for launches behind a device skip flag); that
+ *   launch then synchronises its stream.  0 (the default) uses the cached
+ *   split when there is one, else S = 4.  PTROM_EINVAL for on outside [0, 1].
+ * ptrom_autotune_reset(): forgets every cached split. */
+int ptrom_tune_pairs(int n, int prec, double delta, ptrom_stream_t stream);
+int ptrom_set_autotune(int on);
+int ptrom_autotune_reset(void);
+
 /* Instrumentation (host-side, process-wide).
  * ptrom_launch_count: number of CUDA kernels the library has launched so far.
  * ptrom_timing_enable(on): on = 0 stops recording; on = 1 brackets every

@@ -11,6 +11,8 @@
 //   dGamma:    g_t += w_j . e3 x (s_j - t) r / (2 pi)
 // The difference forms make the j == t term vanish identically and avoid the
 // cancellation of D_t v_t against the off-diagonal sum.
+#include <math.h>
+
 #include <vector>
 
 #include "internal.h"
@@ -462,4 +464,36 @@ extern "C" int bs_vjp(int n, const double *x, const double *Gamma, double delta,
     if (!x || !Gamma || !w) return set_error(PTROM_EINVAL, "bs_vjp: NULL array");
     if (!gx_out && !gGamma_out) return PTROM_OK;
     return vjp(n, x, Gamma, delta, w, gx_out, gGamma_out, prec, (cudaStream_t)stream);
+}
+
+extern "C" int ptrom_tune_pairs(int n, int prec, double delta, ptrom_stream_t stream) {
+    using namespace ptrom;
+    PTROM_TRY(check_common("ptrom_tune_pairs", n, n, delta, prec));
+    if (n < 2) return set_error(PTROM_EINVAL, "ptrom_tune_pairs: n must be >= 2");
+    cudaStream_t st = (cudaStream_t)stream;
+    // synthetic bodies: a jittered lattice in the unit square, Gamma = 1/n, v = w = x;
+    // kernel times do not depend on the values
+    std::vector<double> h((size_t)2 * n + n);
+    const int m = (int)ceil(sqrt((double)n));
+    for (int i = 0; i < n; ++i) {
+        h[i] = (i % m + 0.37 * ((i * 7919) % 13) / 13.0) / m;
+        h[n + i] = (i / m + 0.41 * ((i * 104729) % 17) / 17.0) / m;
+        h[2 * (size_t)n + i] = 1.0 / n;
+    }
+    double *d = nullptr;
+    PTROM_TRY(scratch_alloc((void **)&d, sizeof(double) * ((size_t)2 * n + n + (size_t)2 * n + 3 * (size_t)n), st));
+    double *x = d, *G = d + 2 * (size_t)n, *out = G + n, *D = out + 2 * (size_t)n;
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st);
+    int s = e == cudaSuccess ? PTROM_OK : check_cuda(e, "ptrom_tune_pairs: upload");
+    LaunchOpts o;
+    o.tune = true;
+    if (s == PTROM_OK) s = velocity(n, x, n, x, G, delta, out, nullptr, prec, st, o);
+    if (s == PTROM_OK) s = velocity(n, x, n, x, G, delta, out, D, prec, st, o);
+    if (s == PTROM_OK) s = jvp(n, x, G, delta, x, out, prec, st, o);
+    if (s == PTROM_OK) s = vjp(n, x, G, delta, x, out, nullptr, prec, st, o);
+    if (s == PTROM_OK) s = vjp(n, x, G, delta, x, out, D, prec, st, o);
+    const int s2 = scratch_free(d, st);
+    if (s == PTROM_OK) s = s2;
+    if (s == PTROM_OK) s = check_cuda(cudaStreamSynchronize(st), "ptrom_tune_pairs");
+    return s;
 }

@@ -28,6 +28,10 @@ int check_cuda(cudaError_t e, const char *what);
 int device_sm_count();
 extern std::atomic<int> g_source_split;  // 0 = automatic
 extern std::atomic<int> g_split_mode;    // 0 = automatic, 1 = cluster combine, 2 = global combine
+extern std::atomic<int> g_autotune;      // 1: tune the all-pairs source split on first use
+// Cached autotuned source split of a pair kernel at (nt, ns); 0 when none.
+int tuned_split(const void *kernel, int nt, int ns);
+void store_tuned_split(const void *kernel, int nt, int ns, int S);
 extern std::atomic<long long> g_launches;  // kernels launched by the library
 inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 // Stream-ordered scratch from a library-owned memory pool per device whose

@@ -38,6 +38,7 @@ struct LaunchOpts {
     LinEpi lin;
     const int *skip = nullptr;
     Slots *slots = nullptr;
+    bool tune = false;  // autotune this launch's split if it has no cached value
 };
 
 int velocity(int nt, const double *xt, int ns, const double *xs, const double *G, double delta,

@@ -427,33 +427,17 @@ inline PairScratchLayout pair_scratch_layout(size_t rec_bytes, int nacc, int tb,
 // per cent of the best S in 1..16 with either combine, and the global combine
 // is 0-4 % faster than the cluster one (its CTAs need not be co-scheduled nor
 // wait for one another).
+// One pack + pair launch with split S and the given combine, on buf (at least
+// pair_scratch_layout(..., S, global).total bytes).
 template <class Op>
-int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t stream, const LaunchOpts &o = {}) {
+cudaError_t launch_pairs_on(const typename Op::Args &args, int nt, int ns, cudaStream_t stream, const LaunchOpts &o,
+                            int S, bool global, char *buf) {
     using Rec = typename Op::Rec;
-    constexpr int NACC = Op::NACC;
     constexpr int TB = op_tb<Op>();
     const int tblocks = (nt + TB - 1) / TB;
     const int nchunks = (ns + kChunk - 1) / kChunk;
     const int ns_pad = nchunks * kChunk;
-    const int forced = o.split > 0 ? o.split : g_source_split.load();
-    const int mode = g_split_mode.load();
-    bool global = mode != 1;
-    int S = forced;
-    if (S <= 0) {
-        S = kAutoSplit;
-        while (S > 1 && nchunks < S * kWarps) --S;
-    }
-    if (global && o.scratch && pair_scratch_layout(sizeof(Rec), NACC, TB, nt, ns, S, true).total > o.scratch_bytes) {
-        if (mode == 2) return set_error(PTROM_ENOMEM, "pair launch: scratch too small for the global combine");
-        global = false;  // the caller's scratch holds the records only
-    }
-    if (!global && S > kMaxCluster)
-        return set_error(PTROM_EINVAL, "pair launch: cluster split %d > %d", S, kMaxCluster);
-    if (S < 1 || S > kMaxSplit) return set_error(PTROM_EINVAL, "bad source split %d", S);
-    const PairScratchLayout L = pair_scratch_layout(sizeof(Rec), NACC, TB, nt, ns, S, global);
-    char *buf = reinterpret_cast<char *>(o.scratch);
-    const bool own = buf == nullptr;
-    if (own) PTROM_TRY(scratch_alloc((void **)&buf, L.total, stream));
+    const PairScratchLayout L = pair_scratch_layout(sizeof(Rec), Op::NACC, TB, nt, ns, S, global);
     Rec *packed = reinterpret_cast<Rec *>(buf + L.rec);
     double *part = (global && S > 1) ? reinterpret_cast<double *>(buf + L.part) : nullptr;
     int *cnt = (global && S > 1) ? reinterpret_cast<int *>(buf + L.cnt) : nullptr;
@@ -483,12 +467,99 @@ int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t str
                                              part, cnt);
     timing_end(slot, stream);
     if (o.slots) o.slots->add(slot);
+    if (e == cudaSuccess) count_launch();
+    return e;
+}
+
+// Autotuning of the global combine's split: every candidate S is launched
+// three times on the caller's data (the first as warm-up) and timed with CUDA
+// events on the stream; the fastest S is cached per (kernel, nt, ns).  The
+// outputs are those of the last launch, which the caller's launch overwrites.
+template <class Op>
+int tune_split(const typename Op::Args &args, int nt, int ns, cudaStream_t stream, const LaunchOpts &o, int *best) {
+    using Rec = typename Op::Rec;
+    constexpr int TB = op_tb<Op>();
+    const int nchunks = (ns + kChunk - 1) / kChunk;
+    static const int cands[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16};
+    const size_t need = pair_scratch_layout(sizeof(Rec), Op::NACC, TB, nt, ns, kMaxSplit, true).total;
+    char *buf = reinterpret_cast<char *>(o.scratch);
+    const bool own = !(buf && o.scratch_bytes >= need);
+    if (own) PTROM_TRY(scratch_alloc((void **)&buf, need, stream));
+    cudaEvent_t ev[2];
+    PTROM_CUDA(cudaEventCreate(&ev[0]));
+    PTROM_CUDA(cudaEventCreate(&ev[1]));
+    float best_ms = -1.f;
+    int bS = 1;
+    cudaError_t e = cudaSuccess;
+    for (int S : cands) {
+        if (S > 1 && nchunks < 8 * S) break;  // every warp keeps a step of 32 records
+        float tmin = -1.f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(ev[0], stream);
+            if (e == cudaSuccess) e = launch_pairs_on<Op>(args, nt, ns, stream, o, S, true, buf);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (rep > 0 && (tmin < 0.f || ms < tmin)) tmin = ms;
+        }
+        if (e != cudaSuccess) break;
+        if (best_ms < 0.f || tmin < best_ms) {
+            best_ms = tmin;
+            bS = S;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    const int s2 = own ? scratch_free(buf, stream) : PTROM_OK;
+    if (e != cudaSuccess) return check_cuda(e, "pair split autotuning");
+    PTROM_TRY(s2);
+    store_tuned_split(reinterpret_cast<const void *>(pair_kernel<Op>), nt, ns, bS);
+    *best = bS;
+    return PTROM_OK;
+}
+
+template <class Op>
+int launch_pairs(const typename Op::Args &args, int nt, int ns, cudaStream_t stream, const LaunchOpts &o = {}) {
+    using Rec = typename Op::Rec;
+    constexpr int NACC = Op::NACC;
+    constexpr int TB = op_tb<Op>();
+    const int nchunks = (ns + kChunk - 1) / kChunk;
+    const int forced = o.split > 0 ? o.split : g_source_split.load();
+    const int mode = g_split_mode.load();
+    bool global = mode != 1;
+    int S = forced;
+    if (S <= 0) {
+        S = kAutoSplit;
+        while (S > 1 && nchunks < S * kWarps) --S;
+        if (global) {
+            const int t = tuned_split(reinterpret_cast<const void *>(pair_kernel<Op>), nt, ns);
+            if (t > 0) {
+                S = t;
+            } else if ((o.tune || g_autotune.load()) && !o.skip) {
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+                    PTROM_TRY(tune_split<Op>(args, nt, ns, stream, o, &S));
+            }
+        }
+    }
+    if (global && o.scratch && pair_scratch_layout(sizeof(Rec), NACC, TB, nt, ns, S, true).total > o.scratch_bytes) {
+        if (mode == 2) return set_error(PTROM_ENOMEM, "pair launch: scratch too small for the global combine");
+        global = false;  // the caller's scratch holds the records only
+    }
+    if (!global && S > kMaxCluster)
+        return set_error(PTROM_EINVAL, "pair launch: cluster split %d > %d", S, kMaxCluster);
+    if (S < 1 || S > kMaxSplit) return set_error(PTROM_EINVAL, "bad source split %d", S);
+    const PairScratchLayout L = pair_scratch_layout(sizeof(Rec), NACC, TB, nt, ns, S, global);
+    char *buf = reinterpret_cast<char *>(o.scratch);
+    const bool own = buf == nullptr;
+    if (own) PTROM_TRY(scratch_alloc((void **)&buf, L.total, stream));
+    const cudaError_t e = launch_pairs_on<Op>(args, nt, ns, stream, o, S, global, buf);
     if (own) {
         const int s2 = scratch_free(buf, stream);
         if (e == cudaSuccess && s2 != PTROM_OK) return s2;
     }
     if (e != cudaSuccess) return check_cuda(e, "pair_kernel launch");
-    count_launch();
     return PTROM_OK;
 }
 

@@ -4,7 +4,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -64,6 +66,36 @@ extern "C" int ptrom_set_source_split(int S) {
 
 namespace ptrom {
 std::atomic<int> g_split_mode{0};
+std::atomic<int> g_autotune{0};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<const void *, int, int, int>, int> g_tuned;  // (kernel, device, nt, ns) -> S
+
+int tuned_split(const void *kernel, int nt, int ns) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tuned.find(std::make_tuple(kernel, dev, nt, ns));
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+void store_tuned_split(const void *kernel, int nt, int ns, int S) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[std::make_tuple(kernel, dev, nt, ns)] = S;
+}
+}  // namespace ptrom
+
+extern "C" int ptrom_set_autotune(int on) {
+    if (on < 0 || on > 1) return ptrom::set_error(PTROM_EINVAL, "ptrom_set_autotune: on=%d outside [0, 1]", on);
+    ptrom::g_autotune.store(on);
+    return PTROM_OK;
+}
+
+extern "C" int ptrom_autotune_reset(void) {
+    std::lock_guard<std::mutex> lk(ptrom::g_tune_mu);
+    ptrom::g_tuned.clear();
+    return PTROM_OK;
 }
 
 extern "C" int ptrom_set_split_mode(int mode) {

@@ -111,6 +111,9 @@ def _load():
         "ptrom_version": ([], _i),
         "ptrom_set_source_split": ([_i], _i),
         "ptrom_set_split_mode": ([_i], _i),
+        "ptrom_tune_pairs": ([_i, _i, _d, _vp], _i),
+        "ptrom_set_autotune": ([_i], _i),
+        "ptrom_autotune_reset": ([], _i),
         "bs_velocity": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_velocity_noalloc": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_jvp": ([_i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
@@ -253,6 +256,20 @@ def set_pod_exact_max(n: int) -> None:
 def set_source_split(S: int) -> None:
     """Force the all-pairs kernels' source split (1..16; 0 = automatic)."""
     _check(lib.ptrom_set_source_split(int(S)))
+
+
+def tune_pairs(n: int, delta: float, prec="fp32c", stream=None) -> None:
+    """Autotune and cache the source split of the n x n all-pairs kernels."""
+    _check(lib.ptrom_tune_pairs(int(n), _prec(prec), float(delta), _stream(stream)))
+
+
+def set_autotune(on: bool) -> None:
+    """Tune every new all-pairs launch shape on first use (off by default)."""
+    _check(lib.ptrom_set_autotune(1 if on else 0))
+
+
+def autotune_reset() -> None:
+    _check(lib.ptrom_autotune_reset())
 
 
 def set_split_mode(mode: int) -> None:

@@ -36,3 +36,16 @@ def model_arrays(case):
     u_s = None if u is None else rom.target_rows(np.asarray(u)[:, None], x0, cl.targets)[0][:, 0]
     return dict(phi_s=Phi_t, x0_s=x0_t, phi_c=cl.Phit, x0_c=cl.x0t, gamma_c=cl.Gt, A=case["A"],
                 off=off, idx=idx, u_s=u_s)
+
+
+def oracle_online_on_library_model(model, Phi, x0, delta, dt, steps, tol=1e-4, max_gn=100, u_inf=None):
+    """The oracle's online Gauss-Newton (Alg. 4 over Alg. 5 HyperPair) run on
+    the library model's own offline pieces (basis, sampled bodies, clusters
+    with their current surrogates, A), so that the online stage alone is
+    compared; returns the reduced trajectory (steps + 1, M)."""
+    q = model.query()
+    c = model.query_clusters()
+    cl = rom.Clusters(c["members"], c["gamma_c"], c["phi_c"], c["x0_c"], c["lists"],
+                      np.asarray(q["sampled"]))
+    red, _ = rom.ptrom_online(cl, Phi, x0, q["A"], delta, dt, steps, tol=tol, max_gn=max_gn, u_inf=u_inf)
+    return red

@@ -51,6 +51,10 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert L.ptrom_set_source_split(17) == -1
     assert L.ptrom_set_split_mode(3) == -1
     assert L.ptrom_set_split_mode(0) == 0
+    assert L.ptrom_set_autotune(2) == -1
+    assert L.ptrom_set_autotune(0) == 0
+    assert L.ptrom_autotune_reset() == 0
+    assert L.ptrom_tune_pairs(1, 0, ctypes.c_double(0.02), None) == -1
     assert L.ptrom_set_source_split(0) == 0
     assert L.ptrom_set_inflow(None, None) == -1
     assert L.ptrom_set_inflow_full(None, None, None) == -1

@@ -220,3 +220,28 @@ def test_jphi_source_splits_are_deterministic(P, split):
         P.set_source_split(0)
     assert torch.equal(a, b)
     assert _rel(a.cpu().numpy(), ref) <= 1e-5
+
+
+def test_autotuned_split_keeps_results(P):
+    """After ptrom_tune_pairs (explicit) and with tuning on first use, every
+    all-pairs kernel still matches the oracle at the tuned shapes."""
+    n = 3002
+    x, G = W.two_cluster(n, seed=67)
+    v = W.random_vectors(x.size, 1, seed=68)[0]
+    P.autotune_reset()
+    try:
+        P.tune_pairs(n, 0.02)
+        f, D = P.bs_velocity(_dev(x), _dev(G), 0.02, selfjac=True)
+        jv = P.bs_jvp(_dev(x), _dev(G), 0.02, _dev(v))
+        fo, Do = direct.velocity(x, G, 0.02, with_selfjac=True)
+        assert _rel(f.cpu().numpy(), fo) <= 1e-5 and _rel(D.cpu().numpy(), Do) <= 1e-5
+        assert _rel(jv.cpu().numpy(), direct.jvp(x, G, 0.02, v)) <= 1e-5
+        P.set_autotune(True)
+        x2, G2 = W.two_cluster(2500, seed=69)
+        f2 = P.bs_velocity(_dev(x2), _dev(G2), 0.02)      # tuned on first use
+        f3 = P.bs_velocity(_dev(x2), _dev(G2), 0.02)      # cached split
+        assert torch.equal(f2, f3)
+        assert _rel(f3.cpu().numpy(), direct.velocity(x2, G2, 0.02)) <= 1e-5
+    finally:
+        P.set_autotune(False)
+        P.autotune_reset()

@@ -9,16 +9,15 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import qoi
+from _ptrom_cases import oracle_online_on_library_model
 from paper_2103_01983_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
 
 def _hamiltonian(x, G, n):
-    X, Y = x[:n], x[n:]
-    d2 = (X[:, None] - X[None, :]) ** 2 + (Y[:, None] - Y[None, :]) ** 2
-    iu = np.triu_indices(n, 1)
-    return -np.sum(G[iu[0]] * G[iu[1]] * np.log(d2[iu])) / (4 * np.pi)
+    return qoi.hamiltonian(x, G)
 
 
 def test_single_vortex_n100_bases_case1():
@@ -48,4 +47,48 @@ def test_single_vortex_n100_bases_case1():
     mae = np.mean(np.hypot(rec[:, :n] - fom[:, :n], rec[:, n:] - fom[:, n:]), axis=1) / l
     aeh = [abs(_hamiltonian(rec[k], G, n) - _hamiltonian(fom[k], G, n)) / abs(_hamiltonian(fom[k], G, n))
            for k in range(0, steps, 100)]
+    # the oracle's online stage on this very model
+    q = model.query()
+    red = oracle_online_on_library_model(model, q["phi"], x0, 0.0, dt, steps, tol=1e-1)
+    rec_o = x0 + red[1:] @ q["phi"].T
+    d = np.mean(np.hypot(rec[:, :n] - rec_o[:, :n], rec[:, n:] - rec_o[:, n:]), axis=1) / l
+    print("CUDA vs oracle PTROM, time-averaged MAE_D:", d.mean())
+    assert d.mean() <= 1e-4, d.mean()
+    assert mae.mean() <= 1e-3 and np.mean(aeh) <= 1e-3, (mae.mean(), np.mean(aeh))
+
+
+@pytest.mark.parametrize("n,M,pc,paper_nc", [(2000, 21, 0.0, 122), (5000, 23, 1.0, 149)])
+def test_single_vortex_larger_cases(n, M, pc, paper_nc):
+    """Table 1's N = 2000 and N = 5000 conditions with the bases-case-1 PTROM
+    (tol 1e-1, M_r = 2M, n_s = M_r) of Table 2 (narrow width, p_c = 0) and
+    Table 3 (moderate width, p_c = 1): N_c near the paper's (122 and 149) and
+    time-averaged QoI errors below 0.1 % (the paper's result for every case).
+    The FOM is FP64 JFNK; its trajectory is the PTROM's training snapshots."""
+    from paper_2103_01983_gb300 import ptrom as P
+    x0, G, dt, steps = W.single_vortex(n)
+    fp = P.fom_params(dt, 0.0, "jfnk", tol=1e-12, prec="fp64", gmres_rtol=1e-10, gmres_max_iter=400)
+    xd = torch.tensor(x0, device="cuda")
+    Gd = torch.tensor(G, device="cuda")
+    x = xd.clone()
+    f = P.bs_velocity(x, Gd, 0.0, prec="fp64")
+    work = P.fom_workspace(fp, n)
+    fom = torch.empty(steps, 2 * n, dtype=torch.float64, device="cuda")
+    for k in range(steps):
+        P.fom_step(fp, Gd, x, f, work=work)
+        fom[k] = x
+    model, info = P.ptrom_build(xd[None], Gd[None], M, 2 * M, 2 * M, steps, fp, criterion="nb", p_c=pc,
+                                tol=1e-1, qr_prec="fp64", snapshots=fom)
+    print(f"N={n}: N_c {info['N_c']} (paper {paper_nc})")
+    assert abs(info["N_c"] - paper_nc) <= 0.25 * paper_nc, info["N_c"]
+    st = model.new_state()
+    hist = torch.zeros(steps, M, dtype=torch.float64, device="cuda")
+    s = P.ptrom_step([model], [st], steps, hist=[hist])
+    assert s["noconv"] == 0
+    fom_h = fom.cpu().numpy()
+    rec = np.array([model.reconstruct(hist[k]).cpu().numpy() for k in range(steps)])
+    l = float(np.hypot(x0[n - 1] - x0[0], x0[2 * n - 1] - x0[n]))
+    mae = np.mean(np.hypot(rec[:, :n] - fom_h[:, :n], rec[:, n:] - fom_h[:, n:]), axis=1) / l
+    aeh = [abs(_hamiltonian(rec[k], G, n) - _hamiltonian(fom_h[k], G, n)) / abs(_hamiltonian(fom_h[k], G, n))
+           for k in range(99, steps, 200)]
+    print(f"N={n}: MAE_D {mae.mean():.2e}, AE_H {np.mean(aeh):.2e}")
     assert mae.mean() <= 1e-3 and np.mean(aeh) <= 1e-3, (mae.mean(), np.mean(aeh))
