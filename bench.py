@@ -815,6 +815,87 @@ def batch_leg(ptrom, dev):
     }
 
 
+def c4_leg(ptrom, dev, count=64, steps=100, k=40, theta=0.5):
+    """The batching configuration's PTROM half: `count` two-cluster instances of
+    uneven N (log-uniform in [4096, 131072], separation and circulation ratio
+    uniform in their ranges, seed 3), each with its own PTROM (k = 40,
+    M_r = n_s = 2k, Barnes-Hut theta, FP64 least squares) trained reproductively
+    on its own `steps`-step GPU FOM trajectory (offline, untimed).  Timed: all
+    instances' online solves in one launch against one launch per instance;
+    reported as PTROM instance-steps (solves) per second beside the GPU FOM's
+    instance-steps per second, with each instance's QoI errors."""
+    import numpy as np
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    ns, seps, ratios = W.batch_instances(count, seed=3)
+    fp = ptrom.fom_params(WORKLOAD["dt"], WORKLOAD["delta"], "jfnk", tol=WORKLOAD["newton_tol"], prec="fp32c")
+    models, rows, refs, fom_ms_total = [], [], [], 0.0
+    t0 = time.perf_counter()
+    for i, (n, sep, ratio) in enumerate(zip(ns, seps, ratios)):
+        n = int(n)
+        x0, G = W.two_cluster(n, seed=i, sep=float(sep), ratio=float(ratio))
+        allx, _, fom_ms = _fom_run(ptrom, fp, x0, G, steps, dev, steps, keep_all=True)
+        fom_ms_total += fom_ms
+        row = {"n": n, "sep": float(sep), "ratio": float(ratio), "fom_ms_per_step": fom_ms}
+        try:
+            model, info = ptrom.ptrom_build(torch.tensor(x0, device=dev)[None], torch.tensor(G, device=dev)[None],
+                                            k, 2 * k, 2 * k, steps, fp, criterion="bh", theta=theta, tol=1e-4,
+                                            qr_prec="fp64", snapshots=allx)
+        except ptrom.PtromError as e:
+            row["error"] = str(e)
+            rows.append(row)
+            continue
+        row["N_c"] = info["N_c"]
+        models.append(model)
+        refs.append((x0, allx[-1].clone(), allx[steps // 2 - 1].clone()))
+        rows.append(row)
+        del allx
+    build_s = time.perf_counter() - t0
+    B = len(models)
+    hists = [torch.zeros(steps, k, dtype=torch.float64, device=dev) for _ in models]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ptrom.ptrom_step(models, [m.new_state(dev) for m in models], 2, want_stats=False)   # warm-up launch
+    sts = [m.new_state(dev) for m in models]
+    torch.cuda.synchronize(dev)
+    e0.record()
+    ptrom.ptrom_step(models, sts, steps, hist=hists, want_stats=False)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    batched_ms = e0.elapsed_time(e1)
+    sts1 = [m.new_state(dev) for m in models]
+    e0.record()
+    for m, st in zip(models, sts1):
+        ptrom.ptrom_step([m], [st], steps, want_stats=False)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    single_ms = e0.elapsed_time(e1)
+    maes = []
+    it = iter(r for r in rows if "error" not in r)
+    for m, h, (x0, x_end, x_mid), r in zip(models, hists, refs, it):
+        n = r["n"]
+        l = float(np.hypot(x0[n - 1] - x0[0], x0[2 * n - 1] - x0[n]))
+        errs = []
+        for xr, kk in ((x_mid, steps // 2 - 1), (x_end, steps - 1)):
+            xp = m.reconstruct(h[kk])
+            errs.append(float(torch.sqrt((xp[:n] - xr[:n]) ** 2 + (xp[n:] - xr[n:]) ** 2).sum()) / (l * n))
+        r["mae_d_mid_end"] = errs
+        maes.append(max(errs))
+    return {
+        "workload": (f"{count} two-cluster instances, N log-uniform in [4096, 131072] (seed 3); each a reproductive "
+                     f"PTROM, k={k}, M_r=n_s={2 * k}, Barnes-Hut theta={theta}, FP64 least squares, "
+                     f"{steps} steps"),
+        "instances_built": B, "build_and_fom_s": build_s,
+        "batched_launch_ms": batched_ms, "per_instance_launches_ms": single_ms,
+        "batched_solves_per_s": B * steps / (batched_ms * 1e-3),
+        "per_instance_solves_per_s": B * steps / (single_ms * 1e-3),
+        "gpu_fom_instance_steps_per_s": count / (fom_ms_total * 1e-3),
+        "mae_d_max": max(maes) if maes else None, "mae_d_mean": float(np.mean(maes)) if maes else None,
+        "instances": rows,
+    }
+
+
 def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5):
     """J Phi (the LSPG basis product) on the two-cluster workload at N = 65536
     with M = 60 random basis columns: library-side events on its launches (the
@@ -979,6 +1060,8 @@ def main():
     ap.add_argument("--single-vortex", action="store_true",
                     help="run only the single-vortex leg (Table 1 conditions, Tables 2-4 settings) and print it")
     ap.add_argument("--sv-n", type=str, default=",".join(map(str, SV_NS)), help="bodies of the --single-vortex leg")
+    ap.add_argument("--c4", action="store_true",
+                    help="run only the batched PTROM leg (64 instances of uneven N, one model each) and print it")
     ap.add_argument("--c3", action="store_true",
                     help="run only the parametric PTROM leg (8 training, 4 held-out parameters) and print it")
     ap.add_argument("--c3-n", type=int, default=65536, help="bodies of the --c3 leg")
@@ -999,6 +1082,11 @@ def main():
         from paper_2103_01983_gb300 import ptrom
         ns = tuple(int(v) for v in args.sv_n.split(","))
         print(json.dumps({"single_vortex": single_vortex_leg(ptrom, torch.device("cuda", 0), ns=ns)}), flush=True)
+        return
+    if args.c4:
+        import torch
+        from paper_2103_01983_gb300 import ptrom
+        print(json.dumps({"c4": c4_leg(ptrom, torch.device("cuda", 0))}), flush=True)
         return
     if args.c3:
         import torch

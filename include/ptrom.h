@@ -424,7 +424,7 @@ int ptrom_step(ptrom_model *const *models, int batch, void *const *state,
  * All input arrays are DEVICE arrays: x0s [n_params][2n], gammas
  * [n_params][n], and p->u_infs [n_params][2n] (per-parameter superimposed
  * inflow, or NULL; p->fom.u_inf is ignored).  Limits of this build: n_params * steps <= 65536 snapshots
- * of at most 64 GB in all, n <= 65536; the residual snapshots keep up to 10
+ * of at most 64 GB in all, n <= 131072; the residual snapshots keep up to 10
  * Gauss-Newton iterates per step (up to 24 GB), later ones are dropped.
  * Synchronises the stream (the host runs the tree and the small dense
  * algebra).

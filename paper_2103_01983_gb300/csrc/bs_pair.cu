@@ -494,6 +494,9 @@ extern "C" int ptrom_tune_pairs(int n, int prec, double delta, ptrom_stream_t st
     if (s == PTROM_OK) s = vjp(n, x, G, delta, x, out, D, prec, st, o);
     const int s2 = scratch_free(d, st);
     if (s == PTROM_OK) s = s2;
-    if (s == PTROM_OK) s = check_cuda(cudaStreamSynchronize(st), "ptrom_tune_pairs");
+    if (s == PTROM_OK) {
+        const cudaError_t es = cudaStreamSynchronize(st);
+        if (es != cudaSuccess) s = check_cuda(es, "ptrom_tune_pairs");
+    }
     return s;
 }

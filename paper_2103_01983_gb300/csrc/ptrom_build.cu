@@ -1036,7 +1036,7 @@ extern "C" int ptrom_build(const ptrom_build_params *p, int n, int n_params, con
                            const double *gammas, ptrom_model **out, ptrom_build_info *info,
                            ptrom_stream_t stream) {
     if (!p || !x0s || !gammas || !out) return set_error(PTROM_EINVAL, "ptrom_build: NULL argument");
-    if (n < 2 || n > 65536 || n_params < 1 || p->steps < 1 || (long long)n_params * p->steps > 65536 ||
+    if (n < 2 || n > 131072 || n_params < 1 || p->steps < 1 || (long long)n_params * p->steps > 65536 ||
         (double)n_params * p->steps * 2 * n * 8 > 64e9)
         return set_error(PTROM_EINVAL, "ptrom_build: sizes out of range (n=%d params=%d steps=%d)", n, n_params, p->steps);
     if (p->M < 1 || p->M > kMaxM || p->M_r < 1 || p->M_r > kMaxMr || p->n_s < 1 || p->n_s > std::min(kMaxNs, n))

@@ -323,3 +323,28 @@ def test_build_errors_leave_the_library_usable(P):
     assert e.value.status == P.EINVAL
     model, info = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 8, 16, 16, 20, fp, theta=0.5)
     assert info["n_snapshots"] == 20 and model.M == 8
+
+
+def test_build_beyond_65536_bodies(P):
+    """The build takes up to 131072 bodies (the batching configuration's
+    largest instances): a 70000-body reproductive Barnes-Hut model follows
+    its own 8-step FOM trajectory within 0.1 % (MAE_D)."""
+    n, steps = 70000, 8
+    x0, G = W.two_cluster(n, seed=12)
+    fp = P.fom_params(0.005, 0.02, "jfnk", prec="fp32c")
+    model, info = P.ptrom_build(_dev(x0)[None], _dev(G)[None], 8, 16, 16, steps, fp, theta=0.5, tol=1e-6)
+    assert model.n == n and info["n_snapshots"] == steps
+    x, Gt = _dev(x0), _dev(G)
+    f = P.bs_velocity(x, Gt, 0.02)
+    work = P.fom_workspace(fp, n)
+    for _ in range(steps):
+        P.fom_step(fp, Gt, x, f, work=work)
+    st = model.new_state()
+    hist = torch.zeros(steps, 8, dtype=torch.float64, device="cuda")
+    s = P.ptrom_step([model], [st], steps, hist=[hist])
+    assert s["noconv"] == 0
+    rec = model.reconstruct(hist[-1]).cpu().numpy()
+    xe = x.cpu().numpy()
+    l = float(np.hypot(x0[n - 1] - x0[0], x0[2 * n - 1] - x0[n]))
+    mae = float(np.mean(np.hypot(rec[:n] - xe[:n], rec[n:] - xe[n:]))) / l
+    assert mae <= 1e-3, mae

