@@ -1060,6 +1060,7 @@ def main():
     ap.add_argument("--single-vortex", action="store_true",
                     help="run only the single-vortex leg (Table 1 conditions, Tables 2-4 settings) and print it")
     ap.add_argument("--sv-n", type=str, default=",".join(map(str, SV_NS)), help="bodies of the --single-vortex leg")
+    ap.add_argument("--sv-cases", type=str, default="1,2,3,4", help="bases cases of the --single-vortex leg")
     ap.add_argument("--c4", action="store_true",
                     help="run only the batched PTROM leg (64 instances of uneven N, one model each) and print it")
     ap.add_argument("--c3", action="store_true",
@@ -1081,7 +1082,9 @@ def main():
         import torch
         from paper_2103_01983_gb300 import ptrom
         ns = tuple(int(v) for v in args.sv_n.split(","))
-        print(json.dumps({"single_vortex": single_vortex_leg(ptrom, torch.device("cuda", 0), ns=ns)}), flush=True)
+        cases = tuple(int(v) - 1 for v in args.sv_cases.split(","))
+        print(json.dumps({"single_vortex": single_vortex_leg(ptrom, torch.device("cuda", 0), ns=ns, cases=cases)}),
+              flush=True)
         return
     if args.c4:
         import torch

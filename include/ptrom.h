@@ -276,6 +276,29 @@ int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x,
              ptrom_stream_t stream);
 
 /*
+ * fom_steps -- nsteps implicit trapezoid steps (as fom_step, block-diagonal
+ * Newton, p->jac_mode = PTROM_JAC_BLOCKDIAG only) with each step replayed
+ * from one CUDA graph: the step's kernels (per Newton iteration the velocity
+ * and self blocks, then the residual, Newton test and update) are captured
+ * once for `iters` iterations, every kernel after the converged iteration
+ * skips itself through a device flag, and the host reads the steps' status
+ * once at the end instead of once per iteration.  iters: Newton iterations
+ * captured per step (1 .. max_iter + 1), or 0: the first step runs as
+ * fom_step and iters = its velocity evaluations + 2.  A step that does not
+ * converge within iters stops the rollout there (later steps do nothing):
+ * PTROM_ENOCONV with x at that step's last iterate (PTROM_ENAN for a
+ * non-finite residual); *steps_done (optional) counts the converged steps.
+ * stats (optional) sums the steps' counts.  Falls back to step-by-step
+ * fom_step calls where the cooperative Newton kernel does not fit the GPU
+ * and while ptrom_timing_enable is on.  Synchronises the stream at the end.
+ * Errors: as fom_step, plus PTROM_EINVAL for another jac_mode, nsteps < 1
+ * or iters outside [0, max_iter + 1].
+ */
+int fom_steps(const ptrom_fom_params *p, int n, const double *Gamma, double *x, double *f,
+              void *work, size_t work_bytes, int nsteps, int iters, ptrom_fom_stats *stats,
+              int *steps_done, ptrom_stream_t stream);
+
+/*
  * Batched FOM over B independent instances of uneven size (parameter sweeps):
  * bs_velocity_batched evaluates Eq. 2 (optionally with the self blocks) for
  * every instance in ONE pack launch and ONE all-pairs launch (a flattened

@@ -588,8 +588,13 @@ struct NewtonArgs {
     double *f_out;          // f(x) -> f_out when the iteration stops (converged or at the limit)
     double *d;              // mode 2: d := 0 (the GMRES correction)
     unsigned int *counter;  // the non-cooperative reductions' arrival counter
+    const int *skip;        // optional: nonzero at launch -> the kernel does nothing
+    double *iters;          // optional: incremented once per iteration that runs
 };
 __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
+    // every block reads the flag before the grid barrier, and block 0 writes
+    // it only after it, so all blocks take the same branch here
+    if (a.skip && *a.skip) return;
     cg::grid_group grid = cg::this_grid();
     __shared__ double sh[2][kRedThreads / 32];
     __shared__ double tot[2];
@@ -670,6 +675,7 @@ __global__ void __launch_bounds__(kRedThreads) k_newton(NewtonArgs a) {
     const int stop = stop_s;
     const double rn = rn_s, xn = xn_s;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (a.iters) *a.iters += 1.0;
         a.flags[0] = stop != 0;
         a.st[0] = stop;
         a.st[1] = rn;
@@ -1210,6 +1216,27 @@ static int dense_factor(Ctx &c) {
     return PTROM_OK;
 }
 
+bool timing_active();  // status.cu: launches are being event-timed
+
+// Rollout bookkeeping of fom_steps: flags[0] is the skip flag of the step's
+// kernels, flags[1] halts the rest of the rollout.  At a step's start its
+// kernels run unless an earlier step halted; at its end the step's status
+// (stop, |r|, iterations that ran) goes to log[step] and a step that did not
+// converge halts the rest.
+__global__ void k_roll_begin(int *flags, double *iters) {
+    flags[0] = flags[1];
+    *iters = 0.0;
+}
+__global__ void k_roll_end(int *flags, const double *st, const double *iters, double *log, int *step) {
+    if (flags[1]) return;
+    const int s = *step;
+    log[3 * s] = st[0];
+    log[3 * s + 1] = st[1];
+    log[3 * s + 2] = *iters;
+    *step = s + 1;
+    if (st[0] != 1.0) flags[1] = 1;
+}
+
 }  // namespace ptrom
 
 using namespace ptrom;
@@ -1219,12 +1246,12 @@ extern "C" size_t fom_workspace_bytes(const ptrom_fom_params *p, int n) {
     return layout(p, n, nullptr).bytes;
 }
 
-extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x, double *f,
-                        void *work, size_t work_bytes, ptrom_fom_stats *stats, ptrom_stream_t stream) {
+// The solver context of one call (fom_step, fom_steps).
+static int init_ctx(Ctx &c, const char *fn, const ptrom_fom_params *p, int n, const double *Gamma, double *x,
+                    double *f, void *work, size_t work_bytes, ptrom_stream_t stream) {
     PTROM_TRY(validate(p, n));
-    if (!Gamma || !x || !f || !work) return set_error(PTROM_EINVAL, "fom_step: NULL pointer");
-    if (((uintptr_t)work) & 255) return set_error(PTROM_EINVAL, "fom_step: work must be 256-byte aligned");
-    Ctx c{};
+    if (!Gamma || !x || !f || !work) return set_error(PTROM_EINVAL, "%s: NULL pointer", fn);
+    if (((uintptr_t)work) & 255) return set_error(PTROM_EINVAL, "%s: work must be 256-byte aligned", fn);
     c.p = p;
     c.n = n;
     c.n2 = 2 * n;
@@ -1234,14 +1261,20 @@ extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, d
     c.st = (cudaStream_t)stream;
     c.W = layout(p, n, (char *)work);
     if (work_bytes < c.W.bytes)
-        return set_error(PTROM_EINVAL, "fom_step: work has %zu bytes, needs %zu", work_bytes, c.W.bytes);
+        return set_error(PTROM_EINVAL, "%s: work has %zu bytes, needs %zu", fn, work_bytes, c.W.bytes);
     c.grid = (c.n2 + 255) / 256;
     if (c.grid > 4 * device_sm_count()) c.grid = 4 * device_sm_count();
     c.rgrid = red_grid(c.n2);
     c.cgrid = coop_grid(n);
     c.coop = coop_fits(c.cgrid, n);
     c.krylov32 = c.coop && p->prec == PTROM_FP32C && p->gmres_rtol >= 1e-5;
-    PTROM_TRY(host_mailbox(kStatSlots * kStatDoubles, kStatSlots, &c.mb, &c.ev));
+    return host_mailbox(kStatSlots * kStatDoubles, kStatSlots, &c.mb, &c.ev);
+}
+
+extern "C" int fom_step(const ptrom_fom_params *p, int n, const double *Gamma, double *x, double *f,
+                        void *work, size_t work_bytes, ptrom_fom_stats *stats, ptrom_stream_t stream) {
+    Ctx c{};
+    PTROM_TRY(init_ctx(c, "fom_step", p, n, Gamma, x, f, work, work_bytes, stream));
     ptrom_fom_stats local{};
     c.stats = stats ? stats : &local;
     memset(c.stats, 0, sizeof(*c.stats));
@@ -1567,4 +1600,121 @@ extern "C" int fom_step_batched(const ptrom_fom_params *p, int B, const int *n, 
     PTROM_TRY(sc.release());
     PTROM_CUDA(cudaStreamSynchronize(st));
     return status;
+}
+
+extern "C" int fom_steps(const ptrom_fom_params *p, int n, const double *Gamma, double *x, double *f, void *work,
+                         size_t work_bytes, int nsteps, int iters, ptrom_fom_stats *stats, int *steps_done,
+                         ptrom_stream_t stream) {
+    if (steps_done) *steps_done = 0;
+    if (!p) return set_error(PTROM_EINVAL, "fom_steps: NULL params");
+    if (p->jac_mode != PTROM_JAC_BLOCKDIAG)
+        return set_error(PTROM_EINVAL, "fom_steps: graph-captured steps take the block-diagonal Newton only");
+    if (nsteps < 1 || iters < 0 || iters > p->max_iter + 1)
+        return set_error(PTROM_EINVAL, "fom_steps: nsteps=%d must be >= 1 and iters=%d in [0, max_iter + 1]", nsteps,
+                         iters);
+    Ctx c{};
+    PTROM_TRY(init_ctx(c, "fom_steps", p, n, Gamma, x, f, work, work_bytes, stream));
+    ptrom_fom_stats total{}, one{};
+    int done = 0;
+    // iters = 0: the first step, host-driven, tells how many iterations a step takes
+    if (iters == 0) {
+        PTROM_TRY(fom_step(p, n, Gamma, x, f, work, work_bytes, &one, stream));
+        total = one;
+        done = 1;
+        iters = std::min(one.velocity_evals + 2, p->max_iter + 1);
+    }
+    if (done < nsteps && (!c.coop || timing_active())) {
+        // no cooperative Newton kernel at this size, or launches being timed: step by step
+        for (; done < nsteps; ++done) {
+            const int e = fom_step(p, n, Gamma, x, f, work, work_bytes, &one, stream);
+            total.newton_iters += one.newton_iters;
+            total.velocity_evals += one.velocity_evals;
+            total.res_norm = one.res_norm;
+            if (e != PTROM_OK) {
+                if (stats) *stats = total;
+                if (steps_done) *steps_done = done;
+                return e;
+            }
+        }
+    }
+    if (done < nsteps) {
+        Work &W = c.W;
+        const int todo = nsteps - done;
+        char *rb = nullptr;
+        ScratchScope sc(c.st);
+        PTROM_TRY(sc.alloc(&rb, 256 + sizeof(double) * 3 * (size_t)todo));
+        double *itersp = (double *)rb, *log = (double *)(rb + 256);
+        int *stepp = (int *)(rb + 8);
+        PTROM_CUDA(cudaMemsetAsync(rb, 0, 256, c.st));
+        PTROM_CUDA(cudaMemsetAsync(W.flags, 0, 64, c.st));
+        // capture one step on a private stream (the caller's may be the legacy
+        // default stream, which cannot be captured) and replay it on theirs
+        cudaStream_t cs = nullptr;
+        PTROM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int kernels = 2;
+        int status = PTROM_OK;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            Ctx cc = c;
+            cc.st = cs;
+            k_roll_begin<<<1, 1, 0, cs>>>(W.flags, itersp);
+            for (int k = 0; k < iters && status == PTROM_OK; ++k) {
+                const bool refresh = k % p->p_it == 0;
+                LaunchOpts vo;
+                vo.scratch = W.pack;
+                vo.scratch_bytes = W.pack_bytes;
+                vo.skip = W.flags;
+                status = velocity(n, x, n, x, Gamma, p->delta, W.fxi, refresh ? W.D : nullptr, p->prec, cs, vo);
+                NewtonArgs na{n, x, W.xprev, W.fxi, f, p->u_inf, cc.hdt, W.r, W.partials, W.redout, p->tol,
+                              k == p->max_iter, W.flags, W.stat, refresh ? 1 : 0, W.D, W.Mi, 1, W.V, W.z,
+                              k == 0 ? 1 : 0, f, W.d, W.counter, W.flags, itersp};
+                void *args[] = {&na};
+                if (status == PTROM_OK) {
+                    const cudaError_t el = cudaLaunchCooperativeKernel((void *)k_newton, dim3(cc.cgrid),
+                                                                      dim3(kRedThreads), args, 0, cs);
+                    if (el != cudaSuccess) status = check_cuda(el, "fom_steps: Newton kernel capture");
+                }
+                kernels += 3;
+            }
+            k_roll_end<<<1, 1, 0, cs>>>(W.flags, W.stat, itersp, log, stepp);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess && status == PTROM_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        for (int s2 = 0; e == cudaSuccess && status == PTROM_OK && s2 < todo; ++s2) e = cudaGraphLaunch(exec, c.st);
+        if (e == cudaSuccess && status == PTROM_OK) count_launch(kernels * todo);
+        std::vector<double> hlog(3 * (size_t)todo);
+        int nd = 0;
+        if (e == cudaSuccess && status == PTROM_OK) e = cudaMemcpyAsync(&nd, stepp, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+        if (e == cudaSuccess && status == PTROM_OK)
+            e = cudaMemcpyAsync(hlog.data(), log, sizeof(double) * hlog.size(), cudaMemcpyDeviceToHost, c.st);
+        if (e == cudaSuccess && status == PTROM_OK) e = cudaStreamSynchronize(c.st);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (status != PTROM_OK) return status;
+        if (e != cudaSuccess) return check_cuda(e, "fom_steps: graph");
+        PTROM_TRY(sc.release());
+        for (int s2 = 0; s2 < nd; ++s2) {
+            const int it = (int)hlog[3 * s2 + 2];
+            total.velocity_evals += it;
+            total.newton_iters += hlog[3 * s2] == 1.0 ? it - 1 : it;
+            total.res_norm = hlog[3 * s2 + 1];
+        }
+        const int ok = (nd > 0 && hlog[3 * (nd - 1)] != 1.0) ? nd - 1 : nd;
+        done += ok;
+        if (stats) *stats = total;
+        if (steps_done) *steps_done = done;
+        if (ok < todo) {
+            const double stop = nd > 0 ? hlog[3 * (nd - 1)] : 0.0;
+            if (stop == 2.0) return set_error(PTROM_ENAN, "fom_steps: non-finite residual in step %d", done);
+            return set_error(PTROM_ENOCONV, "fom_steps: step %d did not converge in %d captured Newton iterations "
+                                            "(|r| = %.3e)", done, iters, total.res_norm);
+        }
+        return PTROM_OK;
+    }
+    if (stats) *stats = total;
+    if (steps_done) *steps_done = done;
+    return PTROM_OK;
 }

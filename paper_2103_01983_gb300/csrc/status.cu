@@ -114,6 +114,8 @@ static std::vector<int> g_kind;
 static size_t g_used = 0;
 constexpr size_t kMaxTimed = 65536;
 
+bool timing_active() { return g_timing.load(std::memory_order_relaxed) != 0; }
+
 int timing_begin(int kind, cudaStream_t st) {
     const int mask = g_timing.load(std::memory_order_relaxed);
     if (!mask || kind < 0 || kind >= 31 || !(mask & (1 << kind))) return -1;

@@ -143,6 +143,8 @@ def _load():
                               ctypes.POINTER(FomStats), _vp], _i),
         "ptrom_set_pod_exact_max": ([_i], _i),
         "ptrom_greedy_sample": ([_i, _i, _vp, _i, _vp], _i),
+        "fom_steps": ([ctypes.POINTER(FomParams), _i, _vp, _vp, _vp, _vp, ctypes.c_size_t, _i, _i,
+                       ctypes.POINTER(FomStats), ctypes.POINTER(_i), _vp], _i),
         "ptrom_model_query_training": ([_vp] + [ctypes.POINTER(_i)] * 3 + [_vp, _vp], _i),
         "ptrom_model_query_clusters": ([_vp] + [ctypes.POINTER(_i)] * 3 + [_vp] * 7, _i),
         "ptrom_gappy_operator": ([_i, _i, _vp, _i, _vp, _vp], _i),
@@ -370,6 +372,24 @@ def fom_step(params, Gamma, x, f, work=None, stream=None, allow_noconv=False, u_
     _check(status)
     d = st.as_dict()
     d["converged"] = True
+    return d
+
+
+def fom_steps(params, Gamma, x, f, nsteps, iters=0, work=None, stream=None, u_inf=None):
+    """nsteps block-diagonal Newton steps in place on (x, f), each replayed
+    from one captured CUDA graph (iters Newton iterations per step; 0: learnt
+    from a first ordinary step).  Returns the summed stats dict."""
+    n = Gamma.numel()
+    params = _with_inflow(params, u_inf)
+    if work is None:
+        work = fom_workspace(params, n, x.device)
+    st = FomStats()
+    done = _i()
+    _check(lib.fom_steps(ctypes.byref(params), n, _ptr(Gamma), _ptr(x), _ptr(f), ctypes.c_void_p(work.data_ptr()),
+                         work.numel(), int(nsteps), int(iters), ctypes.byref(st), ctypes.byref(done),
+                         _stream(stream)))
+    d = st.as_dict()
+    d["steps_done"] = done.value
     return d
 
 

@@ -279,3 +279,52 @@ def test_batched_fom_rejects_inflow(P):
     f = P.bs_velocity(x, Gt, 0.05, prec="fp64")
     with pytest.raises(PtromError):
         P.fom_step_batched(q, [Gt], [x], [f], [P.fom_workspace(params, 64)])
+
+
+@pytest.mark.parametrize("n,prec", [(4096, "fp32c"), (500, "fp64")])
+def test_graph_captured_steps_match_step_by_step(P, n, prec):
+    """fom_steps replays each block-diagonal Newton step from one captured CUDA
+    graph; the same kernels in the same order give the step-by-step result bit
+    for bit.  The time per step of both forms is printed."""
+    x0, G = W.two_cluster(n, seed=90)
+    params = P.fom_params(0.005, 0.02, "blockdiag", prec=prec)
+    steps = 20
+    Gt = _dev(G)
+    xa, xb = _dev(x0), _dev(x0)
+    fa, fb = P.bs_velocity(xa, Gt, 0.02, prec=prec), P.bs_velocity(xb, Gt, 0.02, prec=prec)
+    wa, wb = P.fom_workspace(params, n), P.fom_workspace(params, n)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    evals = 0
+    for _ in range(steps):
+        evals += P.fom_step(params, Gt, xa, fa, work=wa)["velocity_evals"]
+    e1.record()
+    torch.cuda.synchronize()
+    t_step = e0.elapsed_time(e1) / steps
+    e0.record()
+    st = P.fom_steps(params, Gt, xb, fb, steps, work=wb)
+    e1.record()
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / steps
+    print(f"N={n} {prec}: {t_step * 1e3:.0f} us per step by fom_step, {t_graph * 1e3:.0f} us by graph replay")
+    assert st["steps_done"] == steps
+    assert st["velocity_evals"] == evals
+    assert torch.equal(xa, xb) and torch.equal(fa, fb)
+
+
+def test_graph_captured_steps_stop_at_a_nonconverged_step(P):
+    """With fewer captured iterations than a step needs, the rollout stops at
+    that step with PTROM_ENOCONV and the library stays usable."""
+    n = 1024
+    x0, G = W.two_cluster(n, seed=91)
+    params = P.fom_params(0.005, 0.02, "blockdiag", prec="fp32c")
+    Gt, x = _dev(G), _dev(x0)
+    f = P.bs_velocity(x, Gt, 0.02)
+    with pytest.raises(P.PtromError) as e:
+        P.fom_steps(params, Gt, x, f, 5, iters=1)
+    assert e.value.status == P.ENOCONV
+    x2 = _dev(x0)
+    f2 = P.bs_velocity(x2, Gt, 0.02)
+    st = P.fom_steps(params, Gt, x2, f2, 3)
+    assert st["steps_done"] == 3
