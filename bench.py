@@ -567,12 +567,13 @@ def _fom_run(ptrom, fp, x0, G, steps, dev, every, keep_all=False):
     return allx, ref, e0.elapsed_time(e1) / steps
 
 
-def c3_leg(ptrom, dev, n=65536, steps=1000, ks=(20, 40, 60), mults=(2, 4), theta=0.5, every=25):
+def c3_leg(ptrom, dev, n=65536, steps=1000, ks=(20, 40, 60), mults=(2, 4), thetas=(0.5,), every=25):
     """The parametric PTROM configuration: two-cluster bodies with common random
     numbers, separation in [0.8, 1.2] and circulation ratio in [0.5, 2.0];
     trained (offline, untimed) on the GPU FOM at 8 Latin-hypercube parameters
     (seed 1), queried at 4 held-out ones (seed 2); POD rank k, M_r = 2k,
-    n_s = mult * k sampled bodies, Barnes-Hut theta, FP64 least squares.
+    n_s = mult * k sampled bodies, Barnes-Hut theta (each of thetas), FP64
+    least squares.
     Per configuration and held-out parameter: time-averaged MAE_D and AE_H of
     the PTROM against the GPU FOM, of the best point of the trial manifold
     (the basis alone), and of Tier II on the first training parameter (the
@@ -609,7 +610,7 @@ def c3_leg(ptrom, dev, n=65536, steps=1000, ks=(20, 40, 60), mults=(2, 4), theta
                           "fom_ms": fom_ms, "H": {k: _hamiltonian_gpu(v, Gd, n) for k, v in ref.items()}})
     fom_s = time.perf_counter() - t0
     out = {"workload": (f"two clusters, N={n}, delta={delta}, dt={dt}, {steps} steps; 8 LHS training parameters "
-                        f"(seed 1), 4 held-out (seed 2); M_r = 2k; Barnes-Hut theta={theta}; FP64 least squares; "
+                        f"(seed 1), 4 held-out (seed 2); M_r = 2k; Barnes-Hut theta in {list(thetas)}; FP64 least squares; "
                         f"QoIs time-averaged over every {every}th step against the GPU FOM"),
            "fom_seconds": fom_s, "configs": []}
     l_of = lambda x0: float(np.hypot(x0[n - 1] - x0[0], x0[2 * n - 1] - x0[n]))
@@ -625,54 +626,53 @@ def c3_leg(ptrom, dev, n=65536, steps=1000, ks=(20, 40, 60), mults=(2, 4), theta
             aeh.append(abs(_hamiltonian_gpu(xp, run["Gd"], n) - run["H"][k]) / abs(run["H"][k]))
         return float(np.mean(mae)), float(np.mean(aeh))
 
-    for k in ks:
-        for mult in mults:
-            cfg = {"k": k, "M_r": 2 * k, "n_s": mult * k}
-            t0 = time.perf_counter()
-            try:
-                model, info = ptrom.ptrom_build(X0, GS, k, 2 * k, mult * k, steps, fp, criterion="bh",
-                                                theta=theta, tol=1e-4, qr_prec="fp64", snapshots=S)
-            except ptrom.PtromError as e:
-                cfg["error"] = str(e)
-                out["configs"].append(cfg)
-                continue
-            cfg.update(build_s=time.perf_counter() - t0, N_c=info["N_c"],
-                       mean_clusters_per_sampled_body=info["mean_list"])
-            q = model.query()
-            Phi = torch.tensor(q["phi"], device=dev)
-            t2 = torch.tensor(model.query_training()["tier2"][0], device=dev)
-            x0t = torch.tensor(x0s[0], device=dev)
-            run0 = {"x0": x0s[0], "Gd": GS[0], "ref": train_ref,
-                    "H": {kk: _hamiltonian_gpu(v, GS[0], n) for kk, v in train_ref.items()}}
-            cfg["tier2_train0"] = qois({kk: x0t + Phi @ t2[kk] for kk in train_ref}, run0)
-            rows = []
-            for run in held_runs:
-                x0d = torch.tensor(run["x0"], device=dev)
-                best = {kk: x0d + Phi @ (Phi.T @ (xr - x0d)) for kk, xr in run["ref"].items()}
-                model.set_param_full(x0d, run["Gd"])
-                st = model.new_state(dev)
-                hist = torch.zeros(steps, k, dtype=torch.float64, device=dev)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize(dev)
-                e0.record()
-                stats = ptrom.ptrom_step([model], [st], steps, hist=[hist])
-                e1.record()
-                torch.cuda.synchronize(dev)
-                rom_us = 1e3 * e0.elapsed_time(e1) / steps
-                rec = {kk: model.reconstruct(hist[kk - 1]) for kk in run["ref"]}
-                m_p, h_p = qois(rec, run)
-                m_b, h_b = qois(best, run)
-                within = m_p <= QOI_BOUND and h_p <= QOI_BOUND
-                row = {"sep": run["sep"], "ratio": run["ratio"], "mae_d": m_p, "ae_h": h_p,
-                       "best_mae_d": m_b, "best_ae_h": h_b, "ptrom_us_per_step": rom_us,
-                       "fom_ms_per_step": run["fom_ms"], "gn_iters_per_step": stats["gn_iters"] / steps,
-                       "noconv_steps": stats["noconv"], "within_qoi_bound": within}
-                row["speedup_vs_gpu_fom_step" if within else "step_time_ratio_vs_gpu_fom_outside_qoi_bound"] = \
-                    1e3 * run["fom_ms"] / rom_us
-                rows.append(row)
-            cfg["held_out"] = rows
+    for theta, k, mult in ((t, k_, m) for t in thetas for k_ in ks for m in mults):
+        cfg = {"k": k, "M_r": 2 * k, "n_s": mult * k, "theta": theta}
+        t0 = time.perf_counter()
+        try:
+            model, info = ptrom.ptrom_build(X0, GS, k, 2 * k, mult * k, steps, fp, criterion="bh",
+                                            theta=theta, tol=1e-4, qr_prec="fp64", snapshots=S)
+        except ptrom.PtromError as e:
+            cfg["error"] = str(e)
             out["configs"].append(cfg)
-            del model, Phi
+            continue
+        cfg.update(build_s=time.perf_counter() - t0, N_c=info["N_c"],
+                   mean_clusters_per_sampled_body=info["mean_list"])
+        q = model.query()
+        Phi = torch.tensor(q["phi"], device=dev)
+        t2 = torch.tensor(model.query_training()["tier2"][0], device=dev)
+        x0t = torch.tensor(x0s[0], device=dev)
+        run0 = {"x0": x0s[0], "Gd": GS[0], "ref": train_ref,
+                "H": {kk: _hamiltonian_gpu(v, GS[0], n) for kk, v in train_ref.items()}}
+        cfg["tier2_train0"] = qois({kk: x0t + Phi @ t2[kk] for kk in train_ref}, run0)
+        rows = []
+        for run in held_runs:
+            x0d = torch.tensor(run["x0"], device=dev)
+            best = {kk: x0d + Phi @ (Phi.T @ (xr - x0d)) for kk, xr in run["ref"].items()}
+            model.set_param_full(x0d, run["Gd"])
+            st = model.new_state(dev)
+            hist = torch.zeros(steps, k, dtype=torch.float64, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record()
+            stats = ptrom.ptrom_step([model], [st], steps, hist=[hist])
+            e1.record()
+            torch.cuda.synchronize(dev)
+            rom_us = 1e3 * e0.elapsed_time(e1) / steps
+            rec = {kk: model.reconstruct(hist[kk - 1]) for kk in run["ref"]}
+            m_p, h_p = qois(rec, run)
+            m_b, h_b = qois(best, run)
+            within = m_p <= QOI_BOUND and h_p <= QOI_BOUND
+            row = {"sep": run["sep"], "ratio": run["ratio"], "mae_d": m_p, "ae_h": h_p,
+                   "best_mae_d": m_b, "best_ae_h": h_b, "ptrom_us_per_step": rom_us,
+                   "fom_ms_per_step": run["fom_ms"], "gn_iters_per_step": stats["gn_iters"] / steps,
+                   "noconv_steps": stats["noconv"], "within_qoi_bound": within}
+            row["speedup_vs_gpu_fom_step" if within else "step_time_ratio_vs_gpu_fom_outside_qoi_bound"] = \
+                1e3 * run["fom_ms"] / rom_us
+            rows.append(row)
+        cfg["held_out"] = rows
+        out["configs"].append(cfg)
+        del model, Phi
     return out
 
 
@@ -1067,6 +1067,9 @@ def main():
                     help="run only the parametric PTROM leg (8 training, 4 held-out parameters) and print it")
     ap.add_argument("--c3-n", type=int, default=65536, help="bodies of the --c3 leg")
     ap.add_argument("--c3-steps", type=int, default=1000, help="time steps of the --c3 leg")
+    ap.add_argument("--c3-ks", type=str, default="20,40,60", help="POD ranks k of the --c3 leg")
+    ap.add_argument("--c3-mults", type=str, default="2,4", help="n_s / k of the --c3 leg")
+    ap.add_argument("--c3-thetas", type=str, default="0.5", help="Barnes-Hut thetas of the --c3 leg")
     ap.add_argument("--mushroom", action="store_true",
                     help="also run the paper's mushroom-cloud parametric experiment (about 5 minutes)")
     ap.add_argument("--qr-prec", choices=["fp64", "fp32c"], default="fp64",
@@ -1094,8 +1097,10 @@ def main():
     if args.c3:
         import torch
         from paper_2103_01983_gb300 import ptrom
-        print(json.dumps({"c3": c3_leg(ptrom, torch.device("cuda", 0), n=args.c3_n, steps=args.c3_steps)}),
-              flush=True)
+        lst = lambda t, f: tuple(f(v) for v in t.split(","))
+        print(json.dumps({"c3": c3_leg(ptrom, torch.device("cuda", 0), n=args.c3_n, steps=args.c3_steps,
+                                       ks=lst(args.c3_ks, int), mults=lst(args.c3_mults, int),
+                                       thetas=lst(args.c3_thetas, float))}), flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -356,8 +356,10 @@ int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *Gamma,
  *   off     [n_s + 1], idx [off[n_s]]: CSR lists, sampled body i interacts
  *                       with clusters idx[off[i] .. off[i+1])
  *   A       [M_r x n_d] row-major: the gappy operator [P Phi_r]^+
- * Limits: M <= 128, M_r <= 256, n_s <= 512, N_c <= 8192 (shared-memory
- * resident per instance).
+ * Limits: M <= 128, M_r <= 256, n_s <= 512, N_c <= 1048576.  The clusters'
+ * current positions x^QT live in the instance's shared memory while they fit
+ * beside the rest (N_c up to several thousand), else in the instance's state
+ * buffer, which ptrom_state_bytes then sizes to hold them.
  * ------------------------------------------------------------------------ */
 typedef struct ptrom_model ptrom_model;
 

@@ -50,8 +50,9 @@ __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~size_t(15)
 // rows / idx: also reserve the staged Phi_s and A^T rows / the 16-bit cluster
 // lists (nlist entries), constant for the whole launch and read every
 // Gauss-Newton iteration.
+// xqg: x^QT and Gamma~ stay in global memory (no shared-memory room for them).
 __host__ __device__ inline SmemLayout smem_layout(int ns, int M, int Mr, int Nc, int Mp, int Mrp, int qr64,
-                                                  int rows = 0, int idx = 0, int nlist = 0) {
+                                                  int rows = 0, int idx = 0, int nlist = 0, int xqg = 0) {
     SmemLayout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o += al16(bytes); return at; };
@@ -65,8 +66,8 @@ __host__ __device__ inline SmemLayout smem_layout(int ns, int M, int Mr, int Nc,
     L.fp = take(4 * 2 * (size_t)ns);
     L.r = take(4 * 2 * (size_t)ns);
     L.D = take(4 * 3 * (size_t)ns);
-    L.xq = take(4 * 2 * (size_t)Nc);
-    L.gq = take(4 * (size_t)Nc);
+    L.xq = take(xqg ? 0 : 4 * 2 * (size_t)Nc);
+    L.gq = take(xqg ? 0 : 4 * (size_t)Nc);
     // [A C | A r], column-major, ld = Mrp, column M = rhs: FP64 for the FP64
     // QR (assembled in place), else FP32
     L.Bf = take(qr64 ? 0 : 4 * (size_t)Mrp * (M + 1));
@@ -419,11 +420,15 @@ k_ptrom(const InstArgs *__restrict__ insts, int nsteps, DevStats *stats) {
     extern __shared__ __align__(16) unsigned char sm[];
     const InstArgs &I = insts[blockIdx.x];
     const DevModel m = I.m;
-    const SmemLayout L = smem_layout(m.ns, m.M, m.Mr, m.Nc, m.Mp, m.Mrp, m.qr64, m.cache_rows, m.cache_idx, m.nlist);
+    const SmemLayout L =
+        smem_layout(m.ns, m.M, m.Mr, m.Nc, m.Mp, m.Mrp, m.qr64, m.cache_rows, m.cache_idx, m.nlist, m.xq_global);
     double *xh = (double *)(sm + L.xh), *xp = (double *)(sm + L.xp), *dx = (double *)(sm + L.dx);
     float *xhf = (float *)(sm + L.xhf), *df = (float *)(sm + L.df), *red = (float *)(sm + L.red);
     float *f = (float *)(sm + L.f), *fp = (float *)(sm + L.fp), *r = (float *)(sm + L.r), *D = (float *)(sm + L.D);
-    float *xq = (float *)(sm + L.xq), *gq = (float *)(sm + L.gq), *Bf = (float *)(sm + L.Bf);
+    // x^QT in shared memory, or (large N_c) in this instance's state buffer; Gamma~ staged, or read in place
+    float *xq = m.xq_global ? (float *)((char *)I.state + state_base_bytes(m.M, m.ns)) : (float *)(sm + L.xq);
+    float *gqs = (float *)(sm + L.gq), *Bf = (float *)(sm + L.Bf);
+    const float *gq = m.xq_global ? m.gT : gqs;
     double *Bd = (double *)(sm + L.Bd);
     float *Ct = (float *)(sm + L.Ct), *Ats = (float *)(sm + L.Ats);
 
@@ -432,7 +437,8 @@ k_ptrom(const InstArgs *__restrict__ insts, int nsteps, DevStats *stats) {
         xh[k] = st_x[k];
         xp[k] = st_x[k];
     }
-    for (int c = threadIdx.x; c < m.Nc; c += kPT) gq[c] = m.gT[c];
+    if (!m.xq_global)
+        for (int c = threadIdx.x; c < m.Nc; c += kPT) gqs[c] = m.gT[c];
     // constant model rows and lists, read every Gauss-Newton iteration: staged once
     const float *phiB = m.phiB, *At = m.At;
     const unsigned short *idx16 = nullptr;
@@ -622,16 +628,20 @@ extern "C" int ptrom_model_create(const ptrom_model_desc *desc, ptrom_model **ou
     m->oy = s.x0_s[s.n_s];
     d.nlist = L;
     constexpr size_t kSmemCap = 220 * 1024;
-    const SmemLayout lay = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64);
+    // x^QT and Gamma~ in shared memory when they fit, else in global memory
+    d.xq_global = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64).total > kSmemCap ? 1 : 0;
+    const int xg = d.xq_global;
+    const SmemLayout lay = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, 0, 0, 0, xg);
     m->smem = lay.total;
     // stage constant rows / lists in shared memory when they fit
-    if (smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, 1, 0, L).total <= kSmemCap) {
+    if (smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, 1, 0, L, xg).total <= kSmemCap) {
         d.cache_rows = 1;
-        m->smem = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, 1, 0, L).total;
+        m->smem = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, 1, 0, L, xg).total;
     }
-    if (d.Nc <= 65535 && smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, d.cache_rows, 1, L).total <= kSmemCap) {
+    if (d.Nc <= 65535 &&
+        smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, d.cache_rows, 1, L, xg).total <= kSmemCap) {
         d.cache_idx = 1;
-        m->smem = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, d.cache_rows, 1, L).total;
+        m->smem = smem_layout(d.ns, d.M, d.Mr, d.Nc, d.Mp, d.Mrp, d.qr64, d.cache_rows, 1, L, xg).total;
     }
     if (m->smem > kSmemCap) {
         delete m;
@@ -694,7 +704,8 @@ extern "C" int ptrom_set_inflow(ptrom_model *m, const double *u_s) {
 
 extern "C" size_t ptrom_state_bytes(const ptrom_model *m) {
     if (!m) return 0;
-    return ((size_t)(m->d.M + 2 * m->d.ns + 8) * 8 + 255) & ~size_t(255);
+    const size_t base = state_base_bytes(m->d.M, m->d.ns);
+    return m->d.xq_global ? base + ((sizeof(float) * 2 * (size_t)m->d.Nc + 255) & ~size_t(255)) : base;
 }
 
 extern "C" int ptrom_step(ptrom_model *const *models, int batch, void *const *state, double *const *xhat,

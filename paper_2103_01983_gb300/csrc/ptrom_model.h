@@ -9,7 +9,7 @@
 namespace ptrom {
 
 constexpr int kPT = 512;  // threads per instance
-constexpr int kMaxM = 128, kMaxMr = 256, kMaxNs = 512, kMaxNc = 8192;
+constexpr int kMaxM = 128, kMaxMr = 256, kMaxNs = 512, kMaxNc = 1 << 20;
 constexpr int kTileB = 16;  // bodies per A C tile (32 dofs)
 
 struct DevModel {
@@ -27,6 +27,8 @@ struct DevModel {
     int nlist;          // off[ns]: cluster-list entries
     int cache_rows;     // Phi_s and A^T staged in shared memory for the whole launch
     int cache_idx;      // the cluster lists staged in shared memory as 16-bit indices
+    int xq_global;      // x^QT (and Gamma~) too large for shared memory: x^QT lives in the
+                        // instance's state buffer after the state proper, Gamma~ is read from gT
 };
 
 struct InstArgs {
@@ -67,6 +69,9 @@ struct ptrom_model {
 };
 
 namespace ptrom {
+// Bytes of an instance's state proper (xhat, carried velocity, flags), 256-byte
+// aligned; a model with xq_global keeps 2 N_c floats of x^QT after it.
+__host__ __device__ inline size_t state_base_bytes(int M, int ns) { return ((size_t)(M + 2 * ns + 8) * 8 + 255) & ~size_t(255); }
 // Fill the parameter-dependent device arrays of a model from host arrays.
 int model_fill_param(ptrom_model *m, const double *x0_s, const double *phi_c, const double *x0_c,
                      const double *gamma_c);
