@@ -302,6 +302,7 @@ def run_ours(args):
                    "tflops": FLOPS_PER_PAIR[k] * n * n * c / (t * 1e-3) / 1e12}
                for k, (t, c) in ktimes.items() if c and k in FLOPS_PER_PAIR}
     kernels["jphi"] = _jphi_leg(ptrom, dev, flush)
+    kernels["jphi_tc"] = _jphi_leg(ptrom, dev, flush, prec="tf32x3")
     other = _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush)
 
     # end to end: host buffers, H2D of the step's inputs and D2H of its result
@@ -896,10 +897,11 @@ def c4_leg(ptrom, dev, count=64, steps=100, k=40, theta=0.5):
     }
 
 
-def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5):
+def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5, prec="fp32c"):
     """J Phi (the LSPG basis product) on the two-cluster workload at N = 65536
     with M = 60 random basis columns: library-side events on its launches (the
-    source-split sum included), L2 flushed before each."""
+    source-split sum included), L2 flushed before each.  prec "fp32c": FP32
+    pipes; "tf32x3": tensor cores (TF32 hi/lo splits, three products)."""
     import numpy as np
     import torch
 
@@ -910,20 +912,29 @@ def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5):
     Gt = torch.tensor(G, device=dev)
     phi = torch.tensor(np.random.default_rng(5).standard_normal((2 * n, M)) / np.sqrt(2 * n), device=dev)
     for _ in range(2):
-        ptrom.bs_jphi(x, Gt, WORKLOAD["delta"], phi)
+        ptrom.bs_jphi(x, Gt, WORKLOAD["delta"], phi, prec=prec)
     torch.cuda.synchronize(dev)
     ptrom.timing_read()
     ptrom.timing_enable(True, kinds=["jphi"])
     for _ in range(reps):
         flush.zero_()
-        ptrom.bs_jphi(x, Gt, WORKLOAD["delta"], phi)
+        ptrom.bs_jphi(x, Gt, WORKLOAD["delta"], phi, prec=prec)
     torch.cuda.synchronize(dev)
     ptrom.timing_enable(False)
     t, c = ptrom.timing_read()["jphi"]
     flops = 20 + 8 * M  # per pair: the 2x2 block, then 4 multiply-adds per column
     pps = n * n * c / (t * 1e-3)
-    return {"n": n, "M": M, "launches": c, "avg_us": 1e3 * t / c, "pairs_per_s": pps,
-            "flops_per_pair": flops, "tflops": flops * pps / 1e12, "units": "SIMT FP32 pair blocks, FP32 compensated"}
+    out = {"n": n, "M": M, "prec": prec, "launches": c, "avg_us": 1e3 * t / c, "pairs_per_s": pps,
+           "flops_per_pair": flops, "tflops": flops * pps / 1e12}
+    if prec == "tf32x3":
+        npad = 64 * ((M + 63) // 64)
+        # per pair: 3 products (hi hi, hi lo, lo hi) of a 2x2 block with N columns
+        out["units"] = ("tcgen05 kind::tf32 MMAs on pair blocks generated in shared memory, TF32 hi/lo splits, "
+                        "FP32 sums in tensor memory per 256 sources folded into compensated totals")
+        out["tensor_tflops_issued"] = 24 * npad * pps / 1e12
+    else:
+        out["units"] = "SIMT FP32 pair blocks, FP32 compensated"
+    return out
 
 
 def _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush, steps=10):
@@ -1012,7 +1023,8 @@ def _e2e(args, ptrom, params, x0, G, dev, stream, n):
 
 
 def kernel_only(args):
-    """Launch one all-pairs kernel `args.steps` times at N = args.n (for ncu);
+    """Launch one all-pairs kernel `args.steps` times at N = args.n (for ncu;
+    J Phi with M = 60 columns);
     with "ptrom", train the PTROM leg's model (theta 0.5, FP32 QR; untimed)
     and launch the online kernel args.warmup + args.steps times, 10 time
     steps per launch."""
@@ -1036,10 +1048,14 @@ def kernel_only(args):
     x = torch.tensor(x0, device="cuda")
     Gt = torch.tensor(G, device="cuda")
     v = torch.tensor(W.random_vectors(2 * args.n, 1, seed=1)[0], device="cuda")
+    phi = torch.tensor(W.random_vectors(2 * args.n, 60, seed=2).T.copy(), device="cuda") \
+        if args.kernel_only.startswith("jphi") else None
     fn = {"velocity": lambda: ptrom.bs_velocity(x, Gt, 0.02),
           "velocity_selfjac": lambda: ptrom.bs_velocity(x, Gt, 0.02, selfjac=True),
           "jvp": lambda: ptrom.bs_jvp(x, Gt, 0.02, v),
-          "vjp": lambda: ptrom.bs_vjp(x, Gt, 0.02, v)}[args.kernel_only]
+          "vjp": lambda: ptrom.bs_vjp(x, Gt, 0.02, v),
+          "jphi": lambda: ptrom.bs_jphi(x, Gt, 0.02, phi),
+          "jphi_tc": lambda: ptrom.bs_jphi(x, Gt, 0.02, phi, prec="tf32x3")}[args.kernel_only]
     for _ in range(args.warmup + args.steps):
         fn()
     torch.cuda.synchronize()
@@ -1074,7 +1090,7 @@ def main():
                     help="also run the paper's mushroom-cloud parametric experiment (about 5 minutes)")
     ap.add_argument("--qr-prec", choices=["fp64", "fp32c"], default="fp64",
                     help="online least-squares precision of the --vortex-pair / --mushroom legs")
-    ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp", "ptrom"],
+    ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp", "jphi", "jphi_tc", "ptrom"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")
     args = ap.parse_args()

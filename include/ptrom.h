@@ -21,6 +21,10 @@
  *  - Precision `prec`: PTROM_FP32C computes pair terms in FP32 and accumulates
  *    them with compensated (TwoSum) sums; inputs/outputs stay FP64.
  *    PTROM_FP64 computes everything in FP64 (slow on GB300; for checking).
+ *    PTROM_TF32X3 (bs_jphi only; other calls reject it): the contraction
+ *    runs on the tensor cores with each FP32 factor split into TF32 hi + lo
+ *    parts and three products per term (hi*hi + hi*lo + lo*hi); FP32 sums
+ *    in tensor memory over 512 sources at a time, then FP32 sums of those.
  *  - A pair (i, j) whose positions coincide exactly is skipped in every sum:
  *    that is the j != i restriction of Eq. 1 (and a coincident body).
  */
@@ -46,7 +50,7 @@ enum ptrom_status {
     PTROM_ENOMEM = -6    /* a workspace was too small or allocation failed */
 };
 
-enum ptrom_prec { PTROM_FP32C = 0, PTROM_FP64 = 1 };
+enum ptrom_prec { PTROM_FP32C = 0, PTROM_FP64 = 1, PTROM_TF32X3 = 2 };
 
 /* Copies the calling thread's last error message into buf (NUL-terminated,
  * truncated to len) and returns the status it came with. */
@@ -198,7 +202,13 @@ int bs_vjp(int n, const double *x, const double *Gamma, double delta,
  * GNLinearLeastSquares) with the exact kernel Jacobian.
  *   phi, out  [2n x M], column-major (column m is a state-layout vector at
  *             phi + m*2n).  x [2n], Gamma [n].
- * Errors: n < 2, M < 1, delta < 0, NULL arrays, bad prec -> PTROM_EINVAL.
+ *   prec      PTROM_FP32C (FP32 pipes), PTROM_FP64, or PTROM_TF32X3: the sum
+ *             over sources as S_i Phi_i - sum_j K_ij Phi_j (K_ij the pair
+ *             block, S_i = sum_j K_ij), the second term a tensor-core
+ *             contraction whose pair blocks are generated in shared memory;
+ *             this precision synchronises the stream (it reads a status).
+ * Errors: n < 2, M < 1, delta < 0, NULL arrays, bad prec -> PTROM_EINVAL;
+ * PTROM_TF32X3 only: PTROM_ETIMEOUT if a bounded pipeline wait gave up.
  */
 int bs_jphi(int n, const double *x, const double *Gamma, double delta,
             const double *phi, int M, double *out, int prec, ptrom_stream_t stream);
