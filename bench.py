@@ -301,8 +301,9 @@ def run_ours(args):
                    "pairs_per_s": n * n * c / (t * 1e-3),
                    "tflops": FLOPS_PER_PAIR[k] * n * n * c / (t * 1e-3) / 1e12}
                for k, (t, c) in ktimes.items() if c and k in FLOPS_PER_PAIR}
-    kernels["jphi"] = _jphi_leg(ptrom, dev, flush)
-    kernels["jphi_tc"] = _jphi_leg(ptrom, dev, flush, prec="tf32x3")
+    if not args.no_jphi:
+        kernels["jphi"] = _jphi_leg(ptrom, dev, flush)
+        kernels["jphi_tc"] = _jphi_leg(ptrom, dev, flush, prec="tf32x3")
     other = _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush)
 
     # end to end: host buffers, H2D of the step's inputs and D2H of its result
@@ -1071,6 +1072,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ptrom", action="store_true", help="skip the PTROM speed-up leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--no-jphi", action="store_true", help="skip the J Phi kernel legs")
     ap.add_argument("--vortex-pair", action="store_true",
                     help="also run the paper's vortex-pair parametric experiment (about 3 minutes)")
     ap.add_argument("--single-vortex", action="store_true",
