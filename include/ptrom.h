@@ -99,6 +99,14 @@ int ptrom_tune_pairs(int n, int prec, double delta, ptrom_stream_t stream);
 int ptrom_set_autotune(int on);
 int ptrom_autotune_reset(void);
 
+/* Test hook for the tensor-core J Phi's failure path: with on = 1 the next
+ * bs_jphi call with PTROM_TF32X3 withholds its tile copies, so every pipeline
+ * wait in every CTA runs out at its 1 s bound; each CTA then waits (bounded)
+ * for its work in flight, frees its tensor memory and flags the status, and
+ * the call returns PTROM_ETIMEOUT with the stream still usable.  The hook
+ * clears itself after that one call.  PTROM_EINVAL for on outside [0, 1]. */
+int ptrom_test_withhold_jphi_tc(int on);
+
 /* Instrumentation (host-side, process-wide).
  * ptrom_launch_count: number of CUDA kernels the library has launched so far.
  * ptrom_timing_enable(on): on = 0 stops recording; on = 1 brackets every

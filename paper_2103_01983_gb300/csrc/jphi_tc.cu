@@ -34,12 +34,14 @@
 // global time); a CTA that gives up raises a status the host reads, waits
 // (bounded) for its copies and MMAs in flight, and frees its tensor memory.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "scratch.h"
 #include "internal.h"
 
 namespace ptrom {
+std::atomic<int> g_jphi_tc_withhold{0};
 namespace {
 
 constexpr int kTB = 128;       // target bodies per CTA (MMA M = 128 per half)
@@ -274,7 +276,7 @@ __device__ __forceinline__ bool fold_chunk(int c, int sh, uint32_t tmem, uint32_
 template <bool MASK>
 __global__ void __launch_bounds__(kThreads, 1)
 k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const unsigned char *img_all, int ntiles,
-          double *out, double *part, int *status) {
+          double *out, double *part, int *status, int withhold) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tb0 = blockIdx.x * kTB;
@@ -319,7 +321,9 @@ k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const u
     if (warp == kLoadWarp) {
         if (lane == 0) {
             int issued = 0;
-            for (int t = 0; t < T; ++t) {
+            // withhold: the test hook -- no copy is issued, so every wait on
+            // one runs out at its bound and the CTA takes its abort path
+            for (int t = 0; t < (withhold ? 0 : T); ++t) {
                 const int s = t % kStB, use = t / kStB;
                 if (use > 0 && !bar_wait(emptyB + s, (use - 1) & 1, abort_f)) break;
                 bar_expect_tx(bfull + s, kImg);
@@ -520,6 +524,7 @@ int pick_split(int ctas, int ntiles) {
 
 int jphi_tc(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
             cudaStream_t st, int split) {
+    const int withhold = g_jphi_tc_withhold.exchange(0);
     static bool attr_set = false;
     if (!attr_set) {
         PTROM_CUDA(cudaFuncSetAttribute(k_jphi_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
@@ -546,9 +551,11 @@ int jphi_tc(int n, const double *x, const double *G, double delta, const double 
     dim3 grid(tblocks, nslices, S);
     const int slot = timing_begin(PTROM_K_JPHI, st);
     if (delta == 0.0)
-        k_jphi_tc<true><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, out, part, status);
+        k_jphi_tc<true><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, out, part, status,
+                                                       withhold);
     else
-        k_jphi_tc<false><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, out, part, status);
+        k_jphi_tc<false><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, out, part, status,
+                                                        withhold);
     cudaError_t e = cudaGetLastError();
     count_launch();
     if (e == cudaSuccess && S > 1) {
@@ -568,3 +575,9 @@ int jphi_tc(int n, const double *x, const double *G, double delta, const double 
 }
 
 }  // namespace ptrom
+
+extern "C" int ptrom_test_withhold_jphi_tc(int on) {
+    if (on != 0 && on != 1) return ptrom::set_error(PTROM_EINVAL, "ptrom_test_withhold_jphi_tc: on must be 0 or 1");
+    ptrom::g_jphi_tc_withhold.store(on);
+    return PTROM_OK;
+}

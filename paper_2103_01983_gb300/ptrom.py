@@ -115,6 +115,7 @@ def _load():
         "ptrom_tune_pairs": ([_i, _i, _d, _vp], _i),
         "ptrom_set_autotune": ([_i], _i),
         "ptrom_autotune_reset": ([], _i),
+        "ptrom_test_withhold_jphi_tc": ([_i], _i),
         "bs_velocity": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_velocity_noalloc": ([_i, _vp, _i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
         "bs_jvp": ([_i, _vp, _vp, _d, _vp, _vp, _i, _vp], _i),
@@ -273,6 +274,12 @@ def set_autotune(on: bool) -> None:
 
 def autotune_reset() -> None:
     _check(lib.ptrom_autotune_reset())
+
+
+def test_withhold_jphi_tc(on: bool) -> None:
+    """Test hook: the next tensor-core bs_jphi call withholds its tile copies
+    and must come back with PTROM_ETIMEOUT (include/ptrom.h)."""
+    _check(lib.ptrom_test_withhold_jphi_tc(1 if on else 0))
 
 
 def set_split_mode(mode: int) -> None:

@@ -4,15 +4,17 @@ The kernel writes (J Phi)_i = S_i Phi_i - sum_j K_ij Phi_j (K_ij the 2x2 pair
 block of Sec. 2's kernel Jacobian, S_i = sum_j K_ij) and runs the contraction
 on tcgen05 MMAs with TF32 hi/lo splits.  Tolerance: 1e-5 relative (L2 over
 the whole output), the same bar as the FP32 pipes; the 3-term split keeps each
-product to ~2^-20 and no FP32 sum runs over more than 128 MMA steps, so the
-expected error is ~1e-6 (checked against the SIMT kernel too).
+product to ~2^-20 and no hi*hi accumulator in tensor memory takes more than 64
+MMA steps before it is folded into a compensated total, so the expected error
+is ~1e-6 (checked against the SIMT kernel too).
 
 Cases: 128-target blocks with a ragged last block and a ragged last 16-source
-tile, one and two 64-column slices with a ragged last slice (N = 16 .. 64 per
-MMA), delta = 0 (coincidence masking) on a jittered lattice, source splits
-1 .. 7 (partials added in split order: bit-identical run to run), a smooth
-basis (where S_i Phi_i and the contraction partly cancel), and the
-full-size case N = 65536, M = 60 on sampled rows."""
+tile, one to four 64-column slices with a ragged last slice (N = 16 .. 64 per
+MMA), two bodies and one column, delta = 0 (coincidence masking) on a jittered
+lattice with exactly coincident bodies, source splits 1 .. 7 (partials added
+in split order: bit-identical run to run; splits of one tile), a smooth basis
+(where S_i Phi_i and the contraction partly cancel), the full-size case
+N = 65536, M = 60 on sampled rows, and the bounded-wait failure path."""
 import numpy as np
 import pytest
 import torch
@@ -125,3 +127,49 @@ def test_jphi_tf32x3_rejected_elsewhere(P):
         P.bs_velocity(_dev(x), _dev(G), 0.02, prec="tf32x3")
     with pytest.raises(P.PtromError):
         P.bs_jvp(_dev(x), _dev(G), 0.02, _dev(np.ones(2 * n)), prec="tf32x3")
+
+
+@pytest.mark.parametrize("n,M,split", [(2, 1, 0), (130, 256, 0), (130, 61, 7)])
+def test_jphi_tf32x3_edge_shapes(P, n, M, split):
+    """Two bodies and one column (one partly empty tile and target block);
+    four 64-column slices (N = 256 columns); more splits than a split's
+    share of tiles (9 tiles over 7 splits)."""
+    x, G = W.two_cluster(n, seed=79)
+    phi = W.random_vectors(x.size, M, seed=80).T
+    ref = direct.jphi(x, G, 0.02, phi)
+    P.set_source_split(split)
+    try:
+        out = P.bs_jphi(_dev(x), _dev(G), 0.02, _dev(phi), prec="tf32x3").cpu().numpy()
+    finally:
+        P.set_source_split(0)
+    assert _rel(out, ref) <= TOL
+
+
+def test_jphi_tf32x3_coincident_bodies_delta0(P):
+    """delta = 0 with exactly coincident bodies: those pairs are skipped, as
+    in every pair sum of the library and the oracle."""
+    n = 700
+    x, G = _lattice(n, seed=81)
+    x[10], x[n + 10] = x[20], x[n + 20]      # body 10 on body 20
+    x[300], x[n + 300] = x[301], x[n + 301]  # body 300 on body 301
+    phi = W.random_vectors(x.size, 9, seed=82).T
+    ref = direct.jphi(x, G, 0.0, phi)
+    out = P.bs_jphi(_dev(x), _dev(G), 0.0, _dev(phi), prec="tf32x3").cpu().numpy()
+    assert np.all(np.isfinite(out))
+    assert _rel(out, ref) <= TOL
+
+
+def test_jphi_tf32x3_wait_bound_and_recovery(P):
+    """Failure path without a fault: the test hook withholds the tile copies,
+    every CTA's pipeline waits run out at their bound, the call returns
+    PTROM_ETIMEOUT, and the next call on the same context is correct."""
+    n, M = 1000, 20
+    x, G = W.two_cluster(n, seed=83)
+    phi = W.random_vectors(x.size, M, seed=84).T
+    P.test_withhold_jphi_tc(True)
+    with pytest.raises(P.PtromError) as err:
+        P.bs_jphi(_dev(x), _dev(G), 0.02, _dev(phi), prec="tf32x3")
+    assert err.value.status == -5  # PTROM_ETIMEOUT
+    ref = direct.jphi(x, G, 0.02, phi)
+    out = P.bs_jphi(_dev(x), _dev(G), 0.02, _dev(phi), prec="tf32x3").cpu().numpy()
+    assert _rel(out, ref) <= TOL
