@@ -304,6 +304,7 @@ def run_ours(args):
     if not args.no_jphi:
         kernels["jphi"] = _jphi_leg(ptrom, dev, flush)
         kernels["jphi_tc"] = _jphi_leg(ptrom, dev, flush, prec="tf32x3")
+        kernels["jphi_tc_f16"] = _jphi_leg(ptrom, dev, flush, prec="f16x3")
     other = _step_breakdown(ptrom, params, Gt, x, f, work, stream, flush)
 
     # end to end: host buffers, H2D of the step's inputs and D2H of its result
@@ -902,7 +903,8 @@ def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5, prec="fp32c"):
     """J Phi (the LSPG basis product) on the two-cluster workload at N = 65536
     with M = 60 random basis columns: library-side events on its launches (the
     source-split sum included), L2 flushed before each.  prec "fp32c": FP32
-    pipes; "tf32x3": tensor cores (TF32 hi/lo splits, three products)."""
+    pipes; "tf32x3" / "f16x3": tensor cores (TF32 or scaled FP16 hi/lo
+    splits, three products)."""
     import numpy as np
     import torch
 
@@ -927,11 +929,12 @@ def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5, prec="fp32c"):
     pps = n * n * c / (t * 1e-3)
     out = {"n": n, "M": M, "prec": prec, "launches": c, "avg_us": 1e3 * t / c, "pairs_per_s": pps,
            "flops_per_pair": flops, "tflops": flops * pps / 1e12}
-    if prec == "tf32x3":
+    if prec in ("tf32x3", "f16x3"):
         npad = 64 * ((M + 63) // 64)
         # per pair: 3 products (hi hi, hi lo, lo hi) of a 2x2 block with N columns
-        out["units"] = ("tcgen05 kind::tf32 MMAs on pair blocks generated in shared memory, TF32 hi/lo splits, "
-                        "FP32 sums in tensor memory per 256 sources folded into compensated totals")
+        kind = "kind::tf32, TF32" if prec == "tf32x3" else "kind::f16, power-of-two-scaled FP16"
+        out["units"] = (f"tcgen05 {kind} hi/lo splits on pair blocks generated in shared memory, "
+                        "FP32 sums in tensor memory folded every 64 MMA steps into compensated totals")
         out["tensor_tflops_issued"] = 24 * npad * pps / 1e12
     else:
         out["units"] = "SIMT FP32 pair blocks, FP32 compensated"

@@ -23,8 +23,12 @@
  *    PTROM_FP64 computes everything in FP64 (slow on GB300; for checking).
  *    PTROM_TF32X3 (bs_jphi only; other calls reject it): the contraction
  *    runs on the tensor cores with each FP32 factor split into TF32 hi + lo
- *    parts and three products per term (hi*hi + hi*lo + lo*hi); FP32 sums
- *    in tensor memory over 512 sources at a time, then FP32 sums of those.
+ *    parts and three products per term (hi*hi + hi*lo + lo*hi); the hi*hi
+ *    sums run in tensor memory for at most 64 MMA steps, then fold into
+ *    compensated totals.  PTROM_F16X3 (bs_jphi only): the same with FP16
+ *    hi + lo parts (TF32's significand width, twice the K per MMA), the
+ *    factors scaled by powers of two into FP16's range; delta = 0 falls
+ *    back to PTROM_TF32X3.
  *  - A pair (i, j) whose positions coincide exactly is skipped in every sum:
  *    that is the j != i restriction of Eq. 1 (and a coincident body).
  */
@@ -50,7 +54,7 @@ enum ptrom_status {
     PTROM_ENOMEM = -6    /* a workspace was too small or allocation failed */
 };
 
-enum ptrom_prec { PTROM_FP32C = 0, PTROM_FP64 = 1, PTROM_TF32X3 = 2 };
+enum ptrom_prec { PTROM_FP32C = 0, PTROM_FP64 = 1, PTROM_TF32X3 = 2, PTROM_F16X3 = 3 };
 
 /* Copies the calling thread's last error message into buf (NUL-terminated,
  * truncated to len) and returns the status it came with. */
@@ -100,7 +104,7 @@ int ptrom_set_autotune(int on);
 int ptrom_autotune_reset(void);
 
 /* Test hook for the tensor-core J Phi's failure path: with on = 1 the next
- * bs_jphi call with PTROM_TF32X3 withholds its tile copies, so every pipeline
+ * bs_jphi call with PTROM_TF32X3 or PTROM_F16X3 withholds its tile copies, so every pipeline
  * wait in every CTA runs out at its 1 s bound; each CTA then waits (bounded)
  * for its work in flight, frees its tensor memory and flags the status, and
  * the call returns PTROM_ETIMEOUT with the stream still usable.  The hook
@@ -210,13 +214,15 @@ int bs_vjp(int n, const double *x, const double *Gamma, double delta,
  * GNLinearLeastSquares) with the exact kernel Jacobian.
  *   phi, out  [2n x M], column-major (column m is a state-layout vector at
  *             phi + m*2n).  x [2n], Gamma [n].
- *   prec      PTROM_FP32C (FP32 pipes), PTROM_FP64, or PTROM_TF32X3: the sum
- *             over sources as S_i Phi_i - sum_j K_ij Phi_j (K_ij the pair
- *             block, S_i = sum_j K_ij), the second term a tensor-core
- *             contraction whose pair blocks are generated in shared memory;
- *             this precision synchronises the stream (it reads a status).
+ *   prec      PTROM_FP32C (FP32 pipes), PTROM_FP64, or PTROM_TF32X3 /
+ *             PTROM_F16X3: the sum over sources as S_i Phi_i - sum_j K_ij
+ *             Phi_j (K_ij the pair block, S_i = sum_j K_ij), the second term
+ *             a tensor-core contraction whose pair blocks are generated in
+ *             shared memory; these precisions synchronise the stream (they
+ *             read a status).
  * Errors: n < 2, M < 1, delta < 0, NULL arrays, bad prec -> PTROM_EINVAL;
- * PTROM_TF32X3 only: PTROM_ETIMEOUT if a bounded pipeline wait gave up.
+ * PTROM_TF32X3 / PTROM_F16X3 only: PTROM_ETIMEOUT if a bounded pipeline wait
+ * gave up.
  */
 int bs_jphi(int n, const double *x, const double *Gamma, double delta,
             const double *phi, int M, double *out, int prec, ptrom_stream_t stream);

@@ -184,7 +184,8 @@ __global__ void k_jphi64(int n, const double *x, const double *G, double delta, 
 
 int jphi(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out, int prec,
          cudaStream_t st, int split) {
-    if (prec == PTROM_TF32X3) return jphi_tc(n, x, G, delta, phi, M, out, st, split);
+    if (prec == PTROM_TF32X3 || prec == PTROM_F16X3)
+        return jphi_tc(n, x, G, delta, phi, M, out, st, split, prec == PTROM_F16X3);
     if (prec == PTROM_FP64) {
         dim3 grid((n + 127) / 128, M);
         const int slot = timing_begin(PTROM_K_JPHI, st);
@@ -242,7 +243,7 @@ extern "C" int bs_jphi(int n, const double *x, const double *Gamma, double delta
                        double *out, int prec, ptrom_stream_t stream) {
     if (n < 2 || M < 1) return set_error(PTROM_EINVAL, "bs_jphi: need n >= 2 and M >= 1 (n=%d M=%d)", n, M);
     if (!(delta >= 0.0)) return set_error(PTROM_EINVAL, "bs_jphi: delta must be >= 0");
-    if (prec != PTROM_FP32C && prec != PTROM_FP64 && prec != PTROM_TF32X3)
+    if (prec != PTROM_FP32C && prec != PTROM_FP64 && prec != PTROM_TF32X3 && prec != PTROM_F16X3)
         return set_error(PTROM_EINVAL, "bs_jphi: bad prec %d", prec);
     if (!x || !Gamma || !phi || !out) return set_error(PTROM_EINVAL, "bs_jphi: NULL array");
     return jphi(n, x, Gamma, delta, phi, M, out, prec, (cudaStream_t)stream, g_source_split.load());

@@ -1,4 +1,5 @@
-// bs_jphi on the 5th-generation tensor cores (prec PTROM_TF32X3).
+// bs_jphi on the 5th-generation tensor cores (prec PTROM_TF32X3 and
+// PTROM_F16X3).
 //
 // With K the 2n x 2n matrix of pair blocks K_ij = gamma_j A(x_i - x_j)
 // (zero on the block diagonal) and S_i = sum_j K_ij, the J Phi of the LSPG
@@ -9,16 +10,18 @@
 //
 //   * a CTA owns 128 target bodies (MMA rows: their chi dofs in half 0, psi
 //     dofs in half 1) and one slice of up to 64 basis columns (MMA N);
-//   * a tile is 16 source bodies (MMA K = 32: chi dofs, then psi dofs).  A
+//   * a tile is 16 (TF32) or 32 (FP16) source bodies (MMA K = 32 or 64: chi
+//     dofs, then psi dofs; either way 8 groups of 16 bytes per row).  A
 //     loader warp brings each tile's image -- the sources' positions and
-//     gamma, and their Phi rows already split into TF32 hi and lo parts in
-//     the tensor cores' K-major layout -- into shared memory with one bulk
-//     copy (cp.async.bulk, completion on an mbarrier), four tiles ahead;
-//   * eight generator warps evaluate the 2x2 blocks of the tile's 2048 pairs
-//     in FP32, split each entry into TF32 hi + lo, and store them in the same
-//     layout (two stages);
-//   * one thread issues tcgen05.mma kind::tf32 (M = 128, K = 8 per
-//     instruction) for both halves: A_hi B_hi into one accumulator and the
+//     gamma, and their Phi rows already split into hi and lo parts in the
+//     tensor cores' K-major layout -- into shared memory with one bulk copy
+//     (cp.async.bulk, completion on an mbarrier), four tiles ahead;
+//   * eight generator warps evaluate the 2x2 blocks of the tile's pairs in
+//     FP32, split each entry into hi + lo, and store them in the same layout
+//     (two stages);
+//   * one thread issues tcgen05.mma kind::tf32 (K = 8 per instruction) or
+//     kind::f16 (K = 16), M = 128, for both halves: A_hi B_hi into one
+//     accumulator and the
 //     cross terms A_hi B_lo + A_lo B_hi (2^-11 smaller) into another -- the
 //     3-term split that keeps products to ~2^-20 relative -- both in tensor
 //     memory;
@@ -28,6 +31,14 @@
 //     in FP32 never runs over more than 64 MMA steps before it is folded
 //     exactly; the diagonal sums S_i are accumulated per tile in FP32 and
 //     folded into compensated pairs in registers.
+// FP16 has TF32's 11-bit significand but a 5-bit exponent, so that variant
+// scales by powers of two: the blocks by 2^(14 - e) with 2^e bounding
+// 3 max|gamma| / delta (no block entry exceeds it, so nothing overflows;
+// entries far below it lose only absolute bits ~2^-24 of the bound), each
+// basis column by 2^(14 - e_m) from its largest entry; the epilogue divides
+// the powers out exactly.  It needs delta > 0 (the bound); at delta = 0 the
+// call takes the TF32 variant.  Per MMA instruction FP16 moves twice TF32's
+// K, so it issues half as many MMAs per pair.
 // The epilogue forms S_i Phi_i - sum_j K_ij Phi_j in FP64.  Source splits
 // over gridDim.z write FP64 partials that a second kernel adds in split
 // order, as in the SIMT kernel.  Every mbarrier wait is bounded (1 s of
@@ -35,6 +46,8 @@
 // (bounded) for its copies and MMAs in flight, and frees its tensor memory.
 #include <algorithm>
 #include <atomic>
+
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "scratch.h"
@@ -45,7 +58,6 @@ std::atomic<int> g_jphi_tc_withhold{0};
 namespace {
 
 constexpr int kTB = 128;       // target bodies per CTA (MMA M = 128 per half)
-constexpr int kTS = 16;        // source bodies per tile (MMA K = 32)
 constexpr int kNC = 64;        // basis columns per slice (MMA N <= 64)
 constexpr int kChunk = 16;     // tiles accumulated in tensor memory between folds
 constexpr int kStA = 2, kStB = 4;
@@ -57,23 +69,28 @@ constexpr uint32_t kTmemCols = 8 * kNC;  // 512: all of an SM's tensor memory (o
 
 // K-major, no-swizzle operand layout: 8-row x 16-byte core matrices; rows of
 // a core matrix 16 bytes apart, 8-row groups 128 bytes apart (SBO), groups of
-// 4 K elements LBO apart.
+// 16 bytes of K (4 TF32 or 8 FP16 elements) LBO apart; a tile row holds 8
+// such groups in both formats.
 constexpr uint32_t kSbo = 128;
 constexpr uint32_t kALbo = (kTB / 8) * 128;               // 2048
-constexpr uint32_t kATile = 8 * kALbo;                    // 128 rows x 32 K x 4 B = 16 KB
+constexpr uint32_t kATile = 8 * kALbo;                    // 128 rows x 8 K groups = 16 KB
 constexpr uint32_t kAStage = 4 * kATile;                  // (half 0, 1) x (hi, lo)
 constexpr uint32_t kBLbo = (kNC / 8) * 128;               // 1024
-constexpr uint32_t kBTile = 8 * kBLbo;                    // 64 rows x 32 K x 4 B = 8 KB
-constexpr uint32_t kRecBytes = kTS * 16;                  // (x, y, gamma, 0) per source
-constexpr uint32_t kImg = kRecBytes + 2 * kBTile;         // one tile image: 16640 B
+constexpr uint32_t kBTile = 8 * kBLbo;                    // 64 rows x 8 K groups = 8 KB
 constexpr uint32_t kAOff = 0;
 constexpr uint32_t kBOff = kAOff + kStA * kAStage;        // 131072
-constexpr uint32_t kBarOff = kBOff + kStB * kImg;         // 197632
 constexpr int kNumBars = 15;
-constexpr uint32_t kSmem = kBarOff + 256;
+// per format: sources per tile, their records (x, y, gamma, 0), one tile
+// image (records, B hi, B lo), the barrier block, the shared memory
+template <bool F16> __host__ __device__ constexpr int tile_sources() { return F16 ? 32 : 16; }
+template <bool F16> __host__ __device__ constexpr uint32_t rec_bytes() { return tile_sources<F16>() * 16; }
+template <bool F16> __host__ __device__ constexpr uint32_t img_bytes() { return rec_bytes<F16>() + 2 * kBTile; }
+template <bool F16> __host__ __device__ constexpr uint32_t bar_off() { return kBOff + kStB * img_bytes<F16>(); }
+template <bool F16> __host__ __device__ constexpr uint32_t smem_bytes() { return bar_off<F16>() + 256; }
 static_assert(kNumBars * 8 + 8 <= 256, "barrier block");
-static_assert(kImg % 16 == 0 && kBOff % 16 == 0, "bulk copies need 16-byte sizes and addresses");
-static_assert(kSmem <= 227 * 1024, "shared memory");
+static_assert(img_bytes<false>() % 16 == 0 && img_bytes<true>() % 16 == 0 && kBOff % 16 == 0,
+              "bulk copies need 16-byte sizes and addresses");
+static_assert(smem_bytes<false>() <= 227 * 1024 && smem_bytes<true>() <= 227 * 1024, "shared memory");
 static_assert(2 * 128 * 3 * 8 <= kAStage, "S exchange fits in the A stages");
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
@@ -137,18 +154,26 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor, kind::tf32: FP32 accumulate (bits 4-5 = 1), A and B
-// TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at
-// bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+// Instruction descriptor: FP32 accumulate (bits 4-5 = 1), A and B of one
+// type (bits 7-9, 10-12: TF32 = 2 under kind::tf32, FP16 = 0 under
+// kind::f16), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+template <bool F16>
+__host__ __device__ constexpr uint32_t idesc_mma(uint32_t M, uint32_t N) {
+    return (1u << 4) | ((F16 ? 0u : 2u) << 7) | ((F16 ? 0u : 2u) << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+template <bool F16>
+__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (F16)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *b) {
@@ -192,40 +217,86 @@ __device__ __forceinline__ void st4(unsigned char *p, float a, float b, float c,
     *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
 }
 
-// Tile images, per (slice, tile): 16 source records, then Phi rows of the
-// slice's 64 columns (MMA N rows) x the tile's 32 dofs (K), hi then lo.
+// FP16 split of a scaled value: hi rounded to nearest, lo the rounded rest.
+__device__ __forceinline__ void f16_split(float v, __half &hi, __half &lo) {
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// Power-of-two scale 2^(14 - e) for values bounded by x = 2^e .. 2^(e+1)
+// (exponent clamped so the scale stays finite); 1 for x = 0.
+__device__ __forceinline__ int scale_exp(float x) {
+    if (!(x > 0.f)) return 0;
+    int e = (int)((__float_as_uint(x) >> 23) & 0xff) - 127;
+    int se = 14 - e;
+    return se < -120 ? -120 : (se > 120 ? 120 : se);
+}
+
+// Largest |Gamma| (slot 0) and largest |Phi| of each column m (slot 1 + m),
+// as the bit patterns of non-negative floats (ordered like the values).
+__global__ void k_tc_maxabs(int n, const double *G, const double *phi, int M, unsigned *umax) {
+    const int col = blockIdx.y;  // 0 .. M - 1: basis columns; M: Gamma
+    const size_t len = col < M ? 2 * (size_t)n : (size_t)n;
+    const double *src = col < M ? phi + (size_t)col * 2 * n : G;
+    float m = 0.f;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf((float)src[e]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(umax + (col < M ? 1 + col : 0), __float_as_uint(m));
+}
+
+// Tile images, per (slice, tile): the tile's source records, then Phi rows of
+// the slice's 64 columns (MMA N rows) x the tile's dofs (K), hi then lo, in
+// the MMA layout; FP16 rows scaled per column (umax, see k_tc_maxabs).
+template <bool F16>
 __global__ void k_tc_pack(int n, const double *x, const double *G, const double *phi, int M, int nslices, int ntiles,
-                          float *img) {
+                          const unsigned *umax, unsigned char *img) {
+    constexpr int kTSx = tile_sources<F16>();
+    constexpr int kEsz = F16 ? 2 : 4;                        // element bytes
+    constexpr int kPer = 16 / kEsz;                          // K elements per 16-byte group
+    constexpr int kRecWords = (int)rec_bytes<F16>() / 4;
+    constexpr int kPart = (int)kBTile / kEsz;                // elements per B part
+    constexpr int kItems = kRecWords + 2 * kPart;
     const double ox = x[0], oy = x[n];
-    constexpr int kWords = kImg / 4;
-    const size_t total = (size_t)nslices * ntiles * kWords;
+    const size_t total = (size_t)nslices * ntiles * kItems;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int w = (int)(e % kWords);
-        const size_t st = e / kWords;
+        const int w = (int)(e % kItems);
+        const size_t st = e / kItems;
         const int tile = (int)(st % ntiles), slice = (int)(st / ntiles);
-        float v = 0.f;
-        if (w < (int)(kRecBytes / 4)) {
-            const int j = tile * kTS + w / 4, comp = w % 4;
+        unsigned char *base = img + st * img_bytes<F16>();
+        if (w < kRecWords) {
+            const int j = tile * kTSx + w / 4, comp = w % 4;
+            float v = 0.f;
             if (j < n) {
                 if (comp == 0) v = (float)(x[j] - ox);
                 else if (comp == 1) v = (float)(x[n + j] - oy);
                 else if (comp == 2) v = (float)(G[j] * kInv2Pi);
             }
-        } else {
-            const int o = w - (int)(kRecBytes / 4);
-            const int part = o / (int)(kBTile / 4), q = o % (int)(kBTile / 4);
-            // word q = kgroup * (LBO / 4) + row * 4 + k % 4
-            const int kg = q / (int)(kBLbo / 4), rem = q % (int)(kBLbo / 4);
-            const int row = rem / 4, k = kg * 4 + rem % 4;
-            const int j = tile * kTS + (k % kTS), dof = k / kTS;
-            const int m = slice * kNC + row;
-            if (j < n && m < M) {
-                const double d = phi[(size_t)m * 2 * n + (size_t)dof * n + j];
-                const float hi = tf32_hi((float)d);
-                v = part == 0 ? hi : (float)(d - (double)hi);
-            }
+            reinterpret_cast<float *>(base)[w] = v;
+            continue;
         }
-        img[e] = v;
+        const int o = w - kRecWords;
+        const int part = o / kPart, q = o % kPart;
+        // element q = kgroup * (LBO / esize) + row * kPer + k % kPer
+        const int kg = q / ((int)kBLbo / kEsz), rem = q % ((int)kBLbo / kEsz);
+        const int row = rem / kPer, k = kg * kPer + rem % kPer;
+        const int j = tile * kTSx + (k % kTSx), dof = k / kTSx;
+        const int m = slice * kNC + row;
+        const double d = (j < n && m < M) ? phi[(size_t)m * 2 * n + (size_t)dof * n + j] : 0.0;
+        unsigned char *dst = base + rec_bytes<F16>() + part * kBTile;
+        if constexpr (F16) {
+            const float sc = m < M ? ldexpf(1.f, scale_exp(__uint_as_float(umax[1 + m]))) : 1.f;
+            __half hi, lo;
+            f16_split((float)(d * sc), hi, lo);
+            reinterpret_cast<__half *>(dst)[q] = part == 0 ? hi : lo;
+        } else {
+            const float hi = tf32_hi((float)d);
+            reinterpret_cast<float *>(dst)[q] = part == 0 ? hi : (float)(d - (double)hi);
+        }
     }
 }
 
@@ -273,10 +344,12 @@ __device__ __forceinline__ bool fold_chunk(int c, int sh, uint32_t tmem, uint32_
     return true;
 }
 
-template <bool MASK>
+template <bool MASK, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
 k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const unsigned char *img_all, int ntiles,
-          double *out, double *part, int *status, int withhold) {
+          const unsigned *umax, double *out, double *part, int *status, int withhold) {
+    constexpr uint32_t kImg = img_bytes<F16>(), kRecBytes = rec_bytes<F16>(), kBarOff = bar_off<F16>();
+    constexpr int kU = F16 ? 8 : 4;  // sources per 16-byte K group
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tb0 = blockIdx.x * kTB;
@@ -337,7 +410,7 @@ k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const u
         __syncwarp();
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(128, nmma);
+            const uint32_t idesc = idesc_mma<F16>(128, nmma);
             for (int t = 0; t < T; ++t) {
                 const int c = t / kChunk;
                 const bool first = t % kChunk == 0, last = t % kChunk == kChunk - 1 || t == T - 1;
@@ -359,9 +432,9 @@ k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const u
                         const uint64_t ah = sdesc(a0 + (2 * h) * kATile + q * 2 * kALbo, kALbo, kSbo);
                         const uint64_t al = sdesc(a0 + (2 * h + 1) * kATile + q * 2 * kALbo, kALbo, kSbo);
                         const uint32_t acc = (first && q == 0) ? 0u : 1u;
-                        mma_tf32(dm, ah, bh, idesc, acc);
-                        mma_tf32(dx, ah, bl, idesc, acc);
-                        mma_tf32(dx, al, bh, idesc, 1u);
+                        mma_issue<F16>(dm, ah, bh, idesc, acc);
+                        mma_issue<F16>(dx, ah, bl, idesc, acc);
+                        mma_issue<F16>(dx, al, bh, idesc, 1u);
                     }
                 }
                 mma_commit(emptyA + t % kStA);
@@ -382,6 +455,9 @@ k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const u
         const bool tact = ti < n;
         const double ox = x[0], oy = x[n];
         const float tx = tact ? (float)(x[ti] - ox) : 0.f, ty = tact ? (float)(x[n + ti] - oy) : 0.f;
+        // FP16: blocks scaled by 2^eA, 2^eA * 3 max|gamma| / delta < 2^15
+        const int eA = F16 ? scale_exp(3.f * __uint_as_float(umax[0]) * (float)kInv2Pi / delta) : 0;
+        const float sA = ldexpf(1.f, eA);
         CSum2 s0, s1;  // (s00, s01), (s10, -)
         s0.zero();
         s1.zero();
@@ -399,11 +475,11 @@ k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const u
             float p00 = 0.f, p01 = 0.f, p10 = 0.f;
 #pragma unroll
             for (int jj = 0; jj < 2; ++jj) {
-                const int jg = 2 * sh + jj;
-                float d00[4], d01[4], d10[4];
+                const int jg = 2 * sh + jj;  // K group of these kU sources' chi dofs (psi: 4 + jg)
+                float d00[kU], d01[kU], d10[kU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float4 r = rec[4 * jg + u];
+                for (int u = 0; u < kU; ++u) {
+                    const float4 r = rec[kU * jg + u];
                     const float a = tx - r.x, b = ty - r.y;
                     const float d2 = fmaf(a, a, b * b);
                     float rr = rcp_approx(d2 + delta);
@@ -418,24 +494,52 @@ k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const u
                     p01 += d01[u];
                     p10 += d10[u];
                 }
-                float h00[4], h01[4], h10[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    h00[u] = tf32_hi(d00[u]);
-                    h01[u] = tf32_hi(d01[u]);
-                    h10[u] = tf32_hi(d10[u]);
-                }
                 const uint32_t rchi = (uint32_t)jg * kALbo + (uint32_t)i * 16;        // chi-dof K group
                 const uint32_t rpsi = (uint32_t)(4 + jg) * kALbo + (uint32_t)i * 16;  // psi-dof K group
                 // half 0 (target chi rows): [A00 | A01]; half 1 (psi rows): [A10 | -A00]
-                st4(A + 0 * kATile + rchi, h00[0], h00[1], h00[2], h00[3]);
-                st4(A + 0 * kATile + rpsi, h01[0], h01[1], h01[2], h01[3]);
-                st4(A + 2 * kATile + rchi, h10[0], h10[1], h10[2], h10[3]);
-                st4(A + 2 * kATile + rpsi, -h00[0], -h00[1], -h00[2], -h00[3]);
-                st4(A + 1 * kATile + rchi, d00[0] - h00[0], d00[1] - h00[1], d00[2] - h00[2], d00[3] - h00[3]);
-                st4(A + 1 * kATile + rpsi, d01[0] - h01[0], d01[1] - h01[1], d01[2] - h01[2], d01[3] - h01[3]);
-                st4(A + 3 * kATile + rchi, d10[0] - h10[0], d10[1] - h10[1], d10[2] - h10[2], d10[3] - h10[3]);
-                st4(A + 3 * kATile + rpsi, h00[0] - d00[0], h00[1] - d00[1], h00[2] - d00[2], h00[3] - d00[3]);
+                if constexpr (F16) {
+                    uint32_t h[4][4], l[4][4];  // (A00, A01, A10, -A00) x 4 half pairs
+#pragma unroll
+                    for (int u = 0; u < kU; u += 2) {
+                        __half a0h, a0l, a1h, a1l;
+                        const float v0[4] = {d00[u], d01[u], d10[u], -d00[u]};
+                        const float v1[4] = {d00[u + 1], d01[u + 1], d10[u + 1], -d00[u + 1]};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            f16_split(v0[c] * sA, a0h, a0l);
+                            f16_split(v1[c] * sA, a1h, a1l);
+                            h[c][u / 2] = pack_h2(a0h, a1h);
+                            l[c][u / 2] = pack_h2(a0l, a1l);
+                        }
+                    }
+                    auto st16 = [](unsigned char *p, const uint32_t (&w)[4]) {
+                        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+                    };
+                    st16(A + 0 * kATile + rchi, h[0]);
+                    st16(A + 0 * kATile + rpsi, h[1]);
+                    st16(A + 2 * kATile + rchi, h[2]);
+                    st16(A + 2 * kATile + rpsi, h[3]);
+                    st16(A + 1 * kATile + rchi, l[0]);
+                    st16(A + 1 * kATile + rpsi, l[1]);
+                    st16(A + 3 * kATile + rchi, l[2]);
+                    st16(A + 3 * kATile + rpsi, l[3]);
+                } else {
+                    float h00[kU], h01[kU], h10[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        h00[u] = tf32_hi(d00[u]);
+                        h01[u] = tf32_hi(d01[u]);
+                        h10[u] = tf32_hi(d10[u]);
+                    }
+                    st4(A + 0 * kATile + rchi, h00[0], h00[1], h00[2], h00[3]);
+                    st4(A + 0 * kATile + rpsi, h01[0], h01[1], h01[2], h01[3]);
+                    st4(A + 2 * kATile + rchi, h10[0], h10[1], h10[2], h10[3]);
+                    st4(A + 2 * kATile + rpsi, -h00[0], -h00[1], -h00[2], -h00[3]);
+                    st4(A + 1 * kATile + rchi, d00[0] - h00[0], d00[1] - h00[1], d00[2] - h00[2], d00[3] - h00[3]);
+                    st4(A + 1 * kATile + rpsi, d01[0] - h01[0], d01[1] - h01[1], d01[2] - h01[2], d01[3] - h01[3]);
+                    st4(A + 3 * kATile + rchi, d10[0] - h10[0], d10[1] - h10[1], d10[2] - h10[2], d10[3] - h10[3]);
+                    st4(A + 3 * kATile + rpsi, h00[0] - d00[0], h00[1] - d00[1], h00[2] - d00[2], h00[3] - d00[3]);
+                }
             }
             s0.add(f2(p00, p01));
             s1.add(f2(p10, 0.f));
@@ -478,7 +582,8 @@ k_jphi_tc(int n, const double *x, const double *phi, int M, float delta, const u
                     if (m >= M) continue;
                     const double pc = phi[(size_t)m * 2 * n + ti], pp = phi[(size_t)m * 2 * n + n + ti];
                     const double si = sh == 0 ? s00 * pc + s01 * pp : s10 * pc - s00 * pp;
-                    const double sum = (double)__uint_as_float(h[k]) + (double)__uint_as_float(l[k]);
+                    double sum = (double)__uint_as_float(h[k]) + (double)__uint_as_float(l[k]);
+                    if (F16) sum = ldexp(sum, -(eA + scale_exp(__uint_as_float(umax[1 + m]))));
                     dst[(size_t)m * 2 * n + (size_t)sh * n + ti] = si - sum;
                 }
             }
@@ -522,40 +627,53 @@ int pick_split(int ctas, int ntiles) {
 
 }  // namespace
 
-int jphi_tc(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
-            cudaStream_t st, int split) {
-    const int withhold = g_jphi_tc_withhold.exchange(0);
+namespace {
+
+template <bool F16>
+int jphi_tc_run(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
+                cudaStream_t st, int split, int withhold) {
+    constexpr uint32_t kImg = img_bytes<F16>(), kSmem = smem_bytes<F16>();
+    constexpr int kTSx = tile_sources<F16>();
     static bool attr_set = false;
     if (!attr_set) {
-        PTROM_CUDA(cudaFuncSetAttribute(k_jphi_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-        PTROM_CUDA(cudaFuncSetAttribute(k_jphi_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+        PTROM_CUDA(cudaFuncSetAttribute(k_jphi_tc<true, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kSmem));
+        PTROM_CUDA(cudaFuncSetAttribute(k_jphi_tc<false, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kSmem));
         attr_set = true;
     }
     const int nslices = (M + kNC - 1) / kNC;
-    const int ntiles = (n + kTS - 1) / kTS;
+    const int ntiles = (n + kTSx - 1) / kTSx;
     const int tblocks = (n + kTB - 1) / kTB;
     const int S = split > 0 ? std::min(split, ntiles) : pick_split(tblocks * nslices, ntiles);
     unsigned char *img = nullptr;
     double *part = nullptr;
     int *status = nullptr;
+    unsigned *umax = nullptr;
     const size_t len = 2 * (size_t)n * M;
     ScratchScope sc(st);
     PTROM_TRY(sc.alloc(&img, (size_t)kImg * nslices * ntiles));
     PTROM_TRY(sc.alloc(&status, sizeof(int)));
+    if (F16) PTROM_TRY(sc.alloc(&umax, sizeof(unsigned) * (M + 1)));
     if (S > 1) PTROM_TRY(sc.alloc(&part, sizeof(double) * len * S));
     PTROM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-    const size_t words = (size_t)nslices * ntiles * (kImg / 4);
-    const int pgrid = (int)std::min<size_t>((words + 255) / 256, (size_t)8 * device_sm_count());
-    k_tc_pack<<<pgrid, 256, 0, st>>>(n, x, G, phi, M, nslices, ntiles, reinterpret_cast<float *>(img));
+    if (F16) {
+        PTROM_CUDA(cudaMemsetAsync(umax, 0, sizeof(unsigned) * (M + 1), st));
+        k_tc_maxabs<<<dim3(std::min(64, (2 * n + 255) / 256), M + 1), 256, 0, st>>>(n, G, phi, M, umax);
+        count_launch();
+    }
+    const size_t items = (size_t)nslices * ntiles * (rec_bytes<F16>() / 4 + 2 * kBTile / (F16 ? 2 : 4));
+    const int pgrid = (int)std::min<size_t>((items + 255) / 256, (size_t)8 * device_sm_count());
+    k_tc_pack<F16><<<pgrid, 256, 0, st>>>(n, x, G, phi, M, nslices, ntiles, umax, img);
     count_launch();
     dim3 grid(tblocks, nslices, S);
     const int slot = timing_begin(PTROM_K_JPHI, st);
     if (delta == 0.0)
-        k_jphi_tc<true><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, out, part, status,
-                                                       withhold);
+        k_jphi_tc<true, F16><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, umax, out, part,
+                                                            status, withhold);
     else
-        k_jphi_tc<false><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, out, part, status,
-                                                        withhold);
+        k_jphi_tc<false, F16><<<grid, kThreads, kSmem, st>>>(n, x, phi, M, (float)delta, img, ntiles, umax, out,
+                                                             part, status, withhold);
     cudaError_t e = cudaGetLastError();
     count_launch();
     if (e == cudaSuccess && S > 1) {
@@ -572,6 +690,16 @@ int jphi_tc(int n, const double *x, const double *G, double delta, const double 
     PTROM_TRY(sc.release());
     if (h_status) return set_error(PTROM_ETIMEOUT, "bs_jphi: a tensor-core pipeline wait gave up");
     return PTROM_OK;
+}
+
+}  // namespace
+
+int jphi_tc(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
+            cudaStream_t st, int split, int f16) {
+    const int withhold = g_jphi_tc_withhold.exchange(0);
+    // FP16 scales the blocks by a bound that needs delta > 0
+    if (f16 && delta > 0.0) return jphi_tc_run<true>(n, x, G, delta, phi, M, out, st, split, withhold);
+    return jphi_tc_run<false>(n, x, G, delta, phi, M, out, st, split, withhold);
 }
 
 }  // namespace ptrom

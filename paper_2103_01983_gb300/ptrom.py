@@ -21,7 +21,9 @@ LIB_PATH = os.path.join(_HERE, "libptrom.so")
 FP32C = 0
 FP64 = 1
 TF32X3 = 2   # bs_jphi only: tensor cores, TF32 hi/lo splits
-_PREC = {"fp32c": FP32C, "fp64": FP64, "tf32x3": TF32X3, FP32C: FP32C, FP64: FP64, TF32X3: TF32X3}
+F16X3 = 3    # bs_jphi only: tensor cores, scaled FP16 hi/lo splits (delta > 0)
+_PREC = {"fp32c": FP32C, "fp64": FP64, "tf32x3": TF32X3, "f16x3": F16X3, FP32C: FP32C, FP64: FP64, TF32X3: TF32X3,
+         F16X3: F16X3}
 
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -195,7 +197,7 @@ def _prec(p):
     try:
         return _PREC[p]
     except KeyError:
-        raise ValueError(f"prec must be 'fp32c', 'fp64' or 'tf32x3', got {p!r}") from None
+        raise ValueError(f"prec must be 'fp32c', 'fp64', 'tf32x3' or 'f16x3', got {p!r}") from None
 
 
 KERNEL_KINDS = ["velocity", "velocity_selfjac", "jvp", "vjp", "jphi", "ptrom_step", "pack", "fom_vec",
