@@ -1059,7 +1059,8 @@ def kernel_only(args):
           "jvp": lambda: ptrom.bs_jvp(x, Gt, 0.02, v),
           "vjp": lambda: ptrom.bs_vjp(x, Gt, 0.02, v),
           "jphi": lambda: ptrom.bs_jphi(x, Gt, 0.02, phi),
-          "jphi_tc": lambda: ptrom.bs_jphi(x, Gt, 0.02, phi, prec="tf32x3")}[args.kernel_only]
+          "jphi_tc": lambda: ptrom.bs_jphi(x, Gt, 0.02, phi, prec="tf32x3"),
+          "jphi_tc_f16": lambda: ptrom.bs_jphi(x, Gt, 0.02, phi, prec="f16x3")}[args.kernel_only]
     for _ in range(args.warmup + args.steps):
         fn()
     torch.cuda.synchronize()
@@ -1095,7 +1096,8 @@ def main():
                     help="also run the paper's mushroom-cloud parametric experiment (about 5 minutes)")
     ap.add_argument("--qr-prec", choices=["fp64", "fp32c"], default="fp64",
                     help="online least-squares precision of the --vortex-pair / --mushroom legs")
-    ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp", "jphi", "jphi_tc", "ptrom"],
+    ap.add_argument("--kernel-only", choices=["velocity", "velocity_selfjac", "jvp", "vjp", "jphi", "jphi_tc",
+                                              "jphi_tc_f16", "ptrom"],
                     help="profiling aid: launch only this kernel (no JSON metric line)")
     ap.add_argument("--n", type=int, default=16384, help="bodies for --kernel-only")
     args = ap.parse_args()
