@@ -21,11 +21,10 @@
 //     (two stages);
 //   * one thread issues tcgen05.mma kind::tf32 (K = 8 per instruction) or
 //     kind::f16 (K = 16), M = 128, for both halves: A_hi B_hi into one
-//     accumulator and the
-//     cross terms A_hi B_lo + A_lo B_hi (2^-11 smaller) into another -- the
-//     3-term split that keeps products to ~2^-20 relative -- both in tensor
-//     memory;
-//   * every 16 tiles (256 sources) the generators read both accumulators
+//     accumulator and the cross terms A_hi B_lo + A_lo B_hi (2^-11 smaller)
+//     into another -- the 3-term split that keeps products to ~2^-20
+//     relative -- both in tensor memory;
+//   * every 16 tiles (256 or 512 sources) the generators read both accumulators
 //     back with tcgen05.ld and add them to a TwoSum-compensated (hi, lo)
 //     total that also lives in tensor memory (tcgen05.st), so the hi*hi sum
 //     in FP32 never runs over more than 64 MMA steps before it is folded
