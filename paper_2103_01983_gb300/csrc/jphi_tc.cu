@@ -605,19 +605,22 @@ __global__ void k_tc_sum(size_t len, int S, const double *__restrict__ part, dou
     }
 }
 
-// Source splits: the S in 1..8 whose CTAs fill whole waves best (one CTA per
-// SM), each split keeping at least 8 tiles; ties go to fewer splits.
+// Source splits: the S in 1..8 minimising waves x (tiles per split + the
+// epilogue's cost in tiles), one CTA per SM, plus 2 % per extra split for
+// the partials' write and sum.  Every split CTA runs the FP64 epilogue
+// (S_i Phi_i - total over 64 columns), worth ~32 tiles on GB300 (fitted to
+// measured times at N = 8192 .. 65536, M = 60, both formats); a partly
+// filled last wave counts as a whole one.
 int pick_split(int ctas, int ntiles) {
+    constexpr long long kEpiTiles = 32;
     const int sms = device_sm_count();
     int best = 1;
-    double best_score = -1.0;
-    for (int S = 1; S <= 8; ++S) {
-        if (S > 1 && ntiles / S < 8) break;
-        const long long c = (long long)ctas * S;
-        const long long waves = (c + sms - 1) / sms;
-        const double score = (double)c / (double)(waves * sms) - 0.01 * (S - 1);
-        if (score > best_score + 1e-12) {
-            best_score = score;
+    long long best_cost = -1;
+    for (int S = 1; S <= 8 && S <= ntiles; ++S) {
+        const long long waves = ((long long)ctas * S + sms - 1) / sms;
+        const long long cost = waves * ((ntiles + S - 1) / S + kEpiTiles) * (100 + 2 * (S - 1));
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
             best = S;
         }
     }
