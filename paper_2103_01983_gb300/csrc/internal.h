@@ -58,9 +58,8 @@ int velocity_batched(int B, const int *n, const double *const *x, const double *
 // J Phi (jphi.cu); split = source split over gridDim.z (0 = automatic).
 int jphi(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out, int prec,
          cudaStream_t st, int split);
-// J Phi on the tensor cores, TF32 or (f16, delta > 0) FP16 operands split in
-// three (jphi_tc.cu); split as jphi.
+// J Phi on the tensor cores, TF32 split in three (jphi_tc.cu); split as jphi.
 int jphi_tc(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
-            cudaStream_t st, int split, int f16);
+            cudaStream_t st, int split);
 
 }  // namespace ptrom

@@ -20,6 +20,10 @@
 #include "internal.h"
 
 namespace ptrom {
+// J Phi on the tensor cores with FP16 operands (jphi_tc.cu; delta = 0 falls
+// back to TF32); split as jphi.
+int jphi_tc_f16(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
+                cudaStream_t st, int split);
 namespace {
 
 constexpr int kJT = 128;  // targets per CTA
@@ -184,8 +188,8 @@ __global__ void k_jphi64(int n, const double *x, const double *G, double delta, 
 
 int jphi(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out, int prec,
          cudaStream_t st, int split) {
-    if (prec == PTROM_TF32X3 || prec == PTROM_F16X3)
-        return jphi_tc(n, x, G, delta, phi, M, out, st, split, prec == PTROM_F16X3);
+    if (prec == PTROM_TF32X3) return jphi_tc(n, x, G, delta, phi, M, out, st, split);
+    if (prec == PTROM_F16X3) return jphi_tc_f16(n, x, G, delta, phi, M, out, st, split);
     if (prec == PTROM_FP64) {
         dim3 grid((n + 127) / 128, M);
         const int slot = timing_begin(PTROM_K_JPHI, st);

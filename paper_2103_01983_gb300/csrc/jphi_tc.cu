@@ -697,10 +697,16 @@ int jphi_tc_run(int n, const double *x, const double *G, double delta, const dou
 }  // namespace
 
 int jphi_tc(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
-            cudaStream_t st, int split, int f16) {
+            cudaStream_t st, int split) {
+    return jphi_tc_run<false>(n, x, G, delta, phi, M, out, st, split, g_jphi_tc_withhold.exchange(0));
+}
+
+// FP16 operands; the power-of-two scaling of the blocks needs delta > 0, so
+// delta = 0 takes the TF32 variant.
+int jphi_tc_f16(int n, const double *x, const double *G, double delta, const double *phi, int M, double *out,
+                cudaStream_t st, int split) {
     const int withhold = g_jphi_tc_withhold.exchange(0);
-    // FP16 scales the blocks by a bound that needs delta > 0
-    if (f16 && delta > 0.0) return jphi_tc_run<true>(n, x, G, delta, phi, M, out, st, split, withhold);
+    if (delta > 0.0) return jphi_tc_run<true>(n, x, G, delta, phi, M, out, st, split, withhold);
     return jphi_tc_run<false>(n, x, G, delta, phi, M, out, st, split, withhold);
 }
 
