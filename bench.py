@@ -301,6 +301,7 @@ def run_ours(args):
                    "pairs_per_s": n * n * c / (t * 1e-3),
                    "tflops": FLOPS_PER_PAIR[k] * n * n * c / (t * 1e-3) / 1e12}
                for k, (t, c) in ktimes.items() if c and k in FLOPS_PER_PAIR}
+    kernels["at_n65536"] = _pairs_leg(ptrom, dev, flush, peak)
     if not args.no_jphi:
         kernels["jphi"] = _jphi_leg(ptrom, dev, flush)
         kernels["jphi_tc"] = _jphi_leg(ptrom, dev, flush, prec="tf32x3")
@@ -897,6 +898,44 @@ def c4_leg(ptrom, dev, count=64, steps=100, k=40, theta=0.5):
         "mae_d_max": max(maes) if maes else None, "mae_d_mean": float(np.mean(maes)) if maes else None,
         "instances": rows,
     }
+
+
+def _pairs_leg(ptrom, dev, flush, peak, n=65536, reps=5):
+    """The four all-pairs kernels of the FOM step at N = 65536 (two clusters,
+    split autotuned for this shape first): library-side events on their
+    launches, L2 flushed before each; TFLOP/s at the survey's flops per pair
+    and the fraction of the same nominal FP32 peak as the roofline line."""
+    import torch
+
+    from paper_2103_01983_gb300 import workloads as W
+
+    x0, G = W.two_cluster(n, seed=0)
+    x = torch.tensor(x0, device=dev)
+    Gt = torch.tensor(G, device=dev)
+    v = torch.tensor(W.random_vectors(2 * n, 1, seed=1)[0], device=dev)
+    ptrom.tune_pairs(n, WORKLOAD["delta"])
+    calls = {"velocity": lambda: ptrom.bs_velocity(x, Gt, WORKLOAD["delta"]),
+             "velocity_selfjac": lambda: ptrom.bs_velocity(x, Gt, WORKLOAD["delta"], selfjac=True),
+             "jvp": lambda: ptrom.bs_jvp(x, Gt, WORKLOAD["delta"], v),
+             "vjp": lambda: ptrom.bs_vjp(x, Gt, WORKLOAD["delta"], v)}
+    out = {}
+    for kind, fn in calls.items():
+        fn()
+        torch.cuda.synchronize(dev)
+        ptrom.timing_read()
+        ptrom.timing_enable(True, kinds=[kind])
+        for _ in range(reps):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize(dev)
+        ptrom.timing_enable(False)
+        t, c = ptrom.timing_read()[kind]
+        pps = n * n * c / (t * 1e-3)
+        tf = FLOPS_PER_PAIR[kind] * pps / 1e12
+        out[kind] = {"launches": c, "avg_us": 1e3 * t / c, "pairs_per_s": pps, "tflops": tf,
+                     "frac_of_nominal_fp32": tf / peak if peak else None}
+    out["n"] = n
+    return out
 
 
 def _jphi_leg(ptrom, dev, flush, n=65536, M=60, reps=5, prec="fp32c"):
