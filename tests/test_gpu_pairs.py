@@ -222,6 +222,34 @@ def test_jphi_source_splits_are_deterministic(P, split):
     assert _rel(a.cpu().numpy(), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("n", [16384, 65536])
+def test_full_size_sampled_rows_tuned_split(P, n):
+    """The bench's launch configuration: the split autotuned for the shape
+    first (ptrom_tune_pairs, as bench.py does before its warm-up), then every
+    all-pairs output on 256 sampled bodies against the oracle."""
+    x, G = W.two_cluster(n, seed=0)
+    delta = 0.02
+    rows = np.random.default_rng(32).choice(n, 256, replace=False)
+    idx = np.r_[rows, n + rows]
+    v, w = W.random_vectors(x.size, 2, seed=33)
+    P.autotune_reset()
+    try:
+        P.tune_pairs(n, delta)
+        f, D = P.bs_velocity(_dev(x), _dev(G), delta, selfjac=True)
+        fo, Do = direct.velocity(x, G, delta, targets=x[idx], with_selfjac=True)
+        assert _rel(f.cpu().numpy()[idx], fo) <= 1e-5
+        assert _rel(D.cpu().numpy()[:, rows], Do) <= 1e-5
+        assert _rel(P.bs_velocity(_dev(x), _dev(G), delta).cpu().numpy()[idx], fo) <= 1e-5
+        jv = P.bs_jvp(_dev(x), _dev(G), delta, _dev(v)).cpu().numpy()
+        assert _rel(jv[idx], direct.jvp(x, G, delta, v, rows=rows)) <= 1e-5
+        gx, gG = P.bs_vjp(_dev(x), _dev(G), delta, _dev(w))
+        gxo, gGo = direct.vjp(x, G, delta, w, rows=rows)
+        assert _rel(gx.cpu().numpy()[idx], gxo) <= 1e-5
+        assert _rel(gG.cpu().numpy()[rows], gGo) <= 1e-5
+    finally:
+        P.autotune_reset()
+
+
 def test_autotuned_split_keeps_results(P):
     """After ptrom_tune_pairs (explicit) and with tuning on first use, every
     all-pairs kernel still matches the oracle at the tuned shapes."""
