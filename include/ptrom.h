@@ -383,7 +383,12 @@ int fom_adjoint_step(const ptrom_fom_params *p, int n, const double *Gamma,
  * Limits: M <= 128, M_r <= 256, n_s <= 512, N_c <= 1048576.  The clusters'
  * current positions x^QT live in the instance's shared memory while they fit
  * beside the rest (N_c up to several thousand), else in the instance's state
- * buffer, which ptrom_state_bytes then sizes to hold them.
+ * buffer, which ptrom_state_bytes then sizes to hold them.  The rest of the
+ * working set -- [A C | A r] (8 M_r (M + 1) bytes with the FP64 least
+ * squares, 4 M_r (M + 1) with FP32) and the per-sampled-body arrays -- must
+ * fit one CTA's 220 KB of shared memory: M = 128 with M_r = 256 needs the
+ * FP32 least squares (the FP64 one fits up to M_r ~ 160 at M = 128);
+ * otherwise PTROM_EINVAL.
  * ------------------------------------------------------------------------ */
 typedef struct ptrom_model ptrom_model;
 
