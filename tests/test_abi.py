@@ -54,6 +54,14 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert L.ptrom_set_autotune(2) == -1
     assert L.ptrom_set_autotune(0) == 0
     assert L.ptrom_autotune_reset() == 0
+    assert L.ptrom_test_withhold_jphi_tc(2) == -1
+    assert L.ptrom_test_withhold_jphi_tc(0) == 0
+    # bs_jphi: the tensor-core precisions pass the host checks, an unknown one does not
+    assert L.bs_jphi(1, null, null, ctypes.c_double(0.1), null, 4, null, 2, null) == -1   # n < 2
+    assert L.bs_jphi(8, null, null, ctypes.c_double(0.1), null, 4, null, 9, null) == -1   # bad prec
+    assert "prec" in lib.last_error()
+    assert L.bs_jphi(8, null, null, ctypes.c_double(0.1), null, 4, null, 3, null) == -1   # NULL arrays
+    assert "NULL" in lib.last_error()
     assert L.ptrom_tune_pairs(1, 0, ctypes.c_double(0.02), None) == -1
     assert L.ptrom_set_source_split(0) == 0
     assert L.ptrom_set_inflow(None, None) == -1
